@@ -1,0 +1,373 @@
+"""Benchmark of the FS-QRPPA hot path on one GB300 (and N replicas).
+
+Workload (geno_int8): n = 5,000 samples, p = 100,000 int8 genotypes
+Bin(2, MAF), MAF ~ U(0.05, 0.5), standardised on the fly, intercept plus 5
+dense N(0,1) covariates (unpenalised), G = 32 equal feature blocks,
+quantiles tau in {0.1, 0.5, 0.9}, lambda = 0.1 lambda_max(tau). One step =
+the whole hot path for the 3 fits: lambda_max per tau, column statistics,
+eta_g by the power method, and FS-QRPPA (Algorithm 1) from a cold start to
+KKT <= 1e-6. The metric is fits per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle (oracle/) on a bounded sample of
+the same workload. Under torchrun (N > 1) every rank runs an independent
+replica (the method is not sharded across GPUs); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tau x lambda PQR fits/s to KKT<=1e-6"
+UNIT = "fits/s"
+TAUS = [0.1, 0.5, 0.9]
+LAMBDA_FRAC = 0.1
+TOL = 1e-6
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_src_hash: str):
+    """Per-launch DRAM bytes of the column pass from the committed ncu summary,
+    or None when absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "k_col_geno_int8.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != kernel_src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("k_iter.cu", "fsqr_internal.h"):
+        with open(os.path.join(ROOT, "paper_2601_02826_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload():
+    from paper_2601_02826_gb300 import synth
+    return synth.geno_int8()
+
+
+# ------------------------------------------------------------------ GB300 arm
+
+def run_gb300(args, rank, world, local_rank):
+    import torch
+
+    from paper_2601_02826_gb300 import fsqr
+    from paper_2601_02826_gb300.device import upload
+
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fsqr.Context(local_rank, stream.cuda_stream)
+    w = make_workload()
+    with torch.cuda.stream(stream):
+        dw = upload(ctx, w, device=dev)
+    stream.synchronize()
+    B = len(TAUS)
+    bp = w.block_ptr()
+    beta = torch.zeros(B * w.P, dtype=torch.float64, device=dev)
+    z = torch.zeros(B * w.n, dtype=torch.float64, device=dev)
+    th = torch.zeros(B * w.n, dtype=torch.float64, device=dev)
+    mixed = dict(tol=TOL, precision=fsqr.MIXED, digits=4, max_group=B)
+
+    def step(opts, infos_out=None):
+        lam = [LAMBDA_FRAC * ctx.lambda_max(dw.design, dw.y, t, dw.omega) for t in TAUS]
+        rc, infos = ctx.fit_batch(dw.design, dw.y, TAUS, lam, dw.omega, bp, beta, z, th, opts=opts)
+        if infos_out is not None:
+            infos_out.extend(infos)
+        return rc
+
+    for _ in range(args.warmup):
+        step(mixed)
+    ctx.profile(enable=True, reset=True)
+    infos = []
+    dist = world > 1
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clocks:
+        e0.record(stream)
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            rc = step(mixed, infos)
+            assert rc == fsqr.OK, (rc, [i.as_dict() for i in infos[-B:]])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if dist:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile(enable=False)
+    ms_t = torch.tensor([ms], device=dev)
+    if dist:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    fits = B * args.steps * world
+    value = fits / (ms_max / 1e3)
+
+    # roofline of the dominant kernel: the column pass (X~^T theta + prox)
+    col_avg_ms = prof.col_ms / max(1, prof.col_samples)
+    achieved = prof.col_bytes / (col_avg_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = ncu_traffic(kernel_hash())
+
+    # accuracy of the returned fits (their own stop test) and iteration counts
+    iters = [i.iters for i in infos[-B:]]
+    kkts = [i.kkt for i in infos[-B:]]
+
+    # plain FP64 GPU FS-QRPPA: one fit at a time, cold start (comparison)
+    fp64 = None
+    if not args.skip_fp64 and rank == 0:
+        fp_opts = dict(tol=TOL, precision=fsqr.FP64, max_group=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inf64 = []
+        rc = step(fp_opts, inf64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        fp64 = {"value": B / t64, "unit": UNIT, "ms_per_step": t64 * 1e3,
+                "iters": [i.iters for i in inf64], "kkt": [i.kkt for i in inf64],
+                "precision": "fp64", "max_group": 1}
+
+    # end to end through the host-buffer entry point (copies inside the call)
+    e2e = None
+    if not args.skip_e2e:
+        gh = torch.from_numpy(np.ascontiguousarray(w.geno).view(np.uint8)).pin_memory()
+        ch = torch.from_numpy(np.ascontiguousarray(w.cov)).pin_memory()
+        yh = torch.from_numpy(w.y.copy()).pin_memory()
+        oh = torch.from_numpy(w.omega.copy()).pin_memory()
+        bh = torch.zeros(B * w.P, dtype=torch.float64).pin_memory()
+        zh = torch.zeros(B * w.n, dtype=torch.float64).pin_memory()
+        thh = torch.zeros(B * w.n, dtype=torch.float64).pin_memory()
+        dh = ctx.design(w.n, w.p, w.c, w.fmt, gh, w.ld, cov=ch, host=True)
+        lam = [LAMBDA_FRAC * ctx.lambda_max(dw.design, dw.y, t, dw.omega) for t in TAUS]
+        ctx.fit_batch(dh, yh, TAUS, lam, oh, bp, bh, zh, thh, opts=mixed, host=True)  # warm-up
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 3))
+        for _ in range(n_e2e):
+            ctx.fit_batch(dh, yh, TAUS, lam, oh, bp, bh, zh, thh, opts=mixed, host=True)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        h2d = gh.numel() + 8 * (ch.numel() + yh.numel() + oh.numel())
+        d2h = 8 * (bh.numel() + zh.numel() + thh.numel())
+        e2e = {"value": B * n_e2e * world / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h),
+               "note": "fsqr_fit_batch_host from pinned host buffers; lambda from a device call"}
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        cpu = cpu_baseline(w, iters)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8 x int8-digits -> int32, f64 state",
+        "data": "synthetic (seeded Bin(2,MAF) genotypes, heteroscedastic normal noise)",
+        "config": {"workload": "geno_int8", "n": w.n, "p": w.p, "covariates": w.c, "G": len(bp) - 1,
+                   "taus": TAUS, "lambda": "0.1 lambda_max(tau)", "fits_per_step": B,
+                   "precision": "mixed (4 int8 digits)", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (X = 500 MB int8)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_col (column pass: X~^T theta by int8 digit DP4A + beta prox)",
+                     "bytes_per_launch": prof.col_bytes, "avg_launch_ms": col_avg_ms,
+                     "samples": prof.col_samples, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+        "kernels_ms": {"col": col_avg_ms, "xbeta": prof.xb_ms / max(1, prof.xb_samples),
+                       "vec": prof.vec_ms / max(1, prof.vec_samples)},
+        "iters": iters, "kkt": kkts, "iterations_timed": prof.iterations,
+        "gpu_launches": int(prof.kernel_launches),
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "fp64_plain": fp64,
+        "cpu_baseline": cpu,
+        "wall_s": t_wall,
+    }
+    if fp64:
+        out["vs_fp64_plain"] = value / fp64["value"]
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def cpu_baseline(w, iters_needed, sample_iters=40):
+    """The FP64 oracle timed on the host on a bounded sample: Algorithm 1 on the
+    full standardised design for `sample_iters` iterations of one fit, scaled
+    to fits/s with the iteration counts the fits needed."""
+    from oracle import fsqrppa as O
+    g = O.decode_stored(w.geno, w.fmt, w.n)
+    d = O.build_design(g, w.cov)
+    bp = w.block_ptr()
+    mu = O.default_mu(w.y)
+    tau = 0.5
+    lmax = O.lambda_max(d.Xt, w.y, tau, w.omega)
+    lam = LAMBDA_FRAC * lmax * w.omega
+    eta = np.full(len(bp) - 1, 1.0)
+    # eta only changes step sizes, not the cost of an iteration
+    eta = eta * mu * float(w.n)
+    t0 = time.perf_counter()
+    O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=0.0, max_iter=sample_iters, check_every=10, lam_norm=lmax)
+    t = time.perf_counter() - t0
+    s_per_iter = t / sample_iters
+    mean_iters = float(np.mean(iters_needed))
+    return {"value": 1.0 / (s_per_iter * mean_iters), "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": (f"oracle Algorithm 1 (numpy FP64, dense standardised X~ {w.n}x{w.P}) timed for "
+                       f"{sample_iters} iterations of the tau=0.5 fit ({s_per_iter * 1e3:.1f} ms/iter), "
+                       f"scaled by the {mean_iters:.0f} iterations per fit the GPU run needed; "
+                       f"design build excluded; threads = numpy BLAS default")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = make_workload()
+    # iterations per fit of this workload, from a previous GPU measurement when
+    # available; otherwise a conservative constant
+    iters = [args.ref_iters] * len(TAUS)
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    for _ in range(args.steps):
+        cb = cpu_baseline(w, iters, sample_iters=10)
+        vals.append(cb["value"])
+    dt = time.perf_counter() - t0
+    v = statistics.median(vals)
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "geno_int8", "n": w.n, "p": w.p},
+           "impl": "reference",
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": cb["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=3000)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        import torch
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gb300(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * fsqr.h - C ABI of the GB300 FS-QRPPA library: weighted-l1 penalised
+ * quantile regression for p >> n by the feature-splitting proximal point
+ * algorithm (FS-QRPPA) of "Scalable Ultra-High-Dimensional Quantile
+ * Regression with Genomic Applications" (arXiv 2601.02826).
+ *
+ * Problem (Section 1, eq. vanilla_QR with eq. weight_l1_penalty):
+ *
+ *   min_beta (1/n) sum_i rho_tau(y_i - x~_i^T beta) + sum_{j>=1} lambda_j |beta_j|,
+ *   rho_tau(u) = (tau - 1{u<0}) u,  lambda_j = lambda * omega_j,  omega_0 = 0.
+ *
+ * x~_i is row i of the standardised design X~ = [1 | C~ | G~]: column 0 is
+ * the intercept, columns 1..c are dense covariates, columns c+1..c+p the
+ * stored feature (genotype) columns. Every column but the intercept is
+ * standardised on the fly when design.standardize = 1 (Section 7: mean and
+ * population sd over non-missing entries; a missing genotype is imputed by
+ * the column mean, i.e. standardised value 0; a constant column is all 0).
+ * All coefficient vectors below (beta, omega) index these P = 1 + c + p
+ * columns and are on the standardised scale unless stated otherwise.
+ *
+ * Iteration (Section 4, eq. fsppa_update, Algorithm 1) over a partition of
+ * the P columns into G contiguous blocks (eq. decompose_x):
+ *   beta_g <- soft-threshold (eq. beta_update) with step 1/eta_g,
+ *   z      <- pinball prox (eq. z_update) with parameter mu,
+ *   theta  <- theta - mu/(G+1) (2 r^{k+1} - r^k),  r = X~ beta + z - y.
+ *
+ * Stopping test (the paper defers it to an appendix that is not part of the
+ * text; this library's reading): every check_every iterations, on the
+ * current iterate, KKT = max(R_p, R_z, R_b, R_1) <= tol with
+ *   R_p = ||y - X~ beta - z||_inf / (1 + ||y||_inf)
+ *   R_z = max_i dist(n theta_i, d rho_tau(z_i))
+ *   R_b = max_{j>=1} dist((X~^T theta)_j, lambda_j d|beta_j|) / lambda_norm
+ *   R_1 = |sum_i theta_i|
+ * where lambda_norm = lambda_max(tau) (1 if that is 0).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are caller-owned CUDA global memory on the context's
+ *     device; the library never frees them. Host pointers are named so.
+ *   - Every call is ordered on the context's stream and returns after that
+ *     stream has finished the call's work (synchronous), unless stated.
+ *   - Return value: FSQR_OK (0) or an FSQR_E* code; fsqr_last_error() then
+ *     holds a one-line message. On FSQR_EINVAL nothing was launched.
+ *   - Not thread-safe per context; distinct contexts are independent.
+ */
+#ifndef FSQR_H
+#define FSQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FSQR_OK 0
+#define FSQR_EINVAL 1   /* invalid argument (nothing launched) */
+#define FSQR_ENOCONV 2  /* max_iter reached before KKT <= tol; outputs valid */
+#define FSQR_ETIMEOUT 3 /* wall-clock budget (opts.timeout_ms) exhausted; outputs valid */
+#define FSQR_ENUMERIC 4 /* NaN/Inf in inputs or iterates */
+#define FSQR_ECUDA 5    /* a CUDA call failed; message has the CUDA error */
+#define FSQR_ENOMEM 6   /* device workspace allocation failed */
+
+/* ---- storage formats of the p feature columns (SNP-major) -------------- */
+#define FSQR_DENSE_F64 0 /* n doubles per column */
+#define FSQR_INT8 1      /* 1 byte per sample: 0/1/2, any other value = missing */
+#define FSQR_2BIT 2      /* 4 samples per byte, sample i in bits 2*(i%4) of byte i/4;
+                            codes 0/1/2, code 3 = missing */
+
+/* ---- arithmetic of the inner products ----------------------------------- */
+#define FSQR_FP64 0  /* plain FP64 for every product and reduction */
+#define FSQR_MIXED 1 /* X~^T theta from exact integer products: theta split into
+                        int8 digits, genotype x digit dot products accumulated
+                        exactly in int32 (DP4A); FP64 state, FP64 X~ beta and
+                        FP64 reductions. int8 storage only. */
+
+/* ---- starting point ------------------------------------------------------ */
+#define FSQR_WARM_NONE 0  /* beta = 0, z = y, theta = 0 */
+#define FSQR_WARM_GIVEN 1 /* beta, z, theta arrays are read as the start */
+#define FSQR_WARM_PATH 2  /* fsqr_fit_batch only: along each tau's lambda path,
+                             fit l starts from fit l-1's solution (Section 7) */
+
+typedef struct fsqr_ctx fsqr_ctx;
+
+/* Design matrix X = [1 | C | G]; see the column conventions above. */
+typedef struct {
+  int64_t n;              /* samples, >= 1 */
+  int64_t p;              /* stored feature columns, >= 0 */
+  int64_t c;              /* dense covariate columns, >= 0 */
+  int32_t geno_format;    /* FSQR_DENSE_F64 | FSQR_INT8 | FSQR_2BIT */
+  int32_t standardize;    /* 1: standardise covariates and features on the fly; 0: raw */
+  const void *geno;       /* device; column j (0-based) at geno + j*geno_ld bytes;
+                             16-byte aligned; NULL allowed when p == 0 */
+  int64_t geno_ld;        /* bytes per column: multiple of 16, >= bytes for n samples */
+  const double *cov;      /* device; covariate k at cov + k*n; NULL allowed when c == 0 */
+  const double *col_mean; /* device, length c+p, or NULL: computed (one pass over X) */
+  const double *col_sd;   /* device, length c+p, or NULL: computed with col_mean */
+} fsqr_design;
+
+typedef struct {
+  double tol;             /* KKT tolerance; default 1e-6 */
+  int32_t max_iter;       /* default 100000; the run stops at the first stop test
+                             (multiple of check_every) at or after max_iter */
+  int32_t check_every;    /* K: stop test every K iterations; default 10 */
+  double mu;              /* > 0, or <= 0 for the default 1/(n sd(y)) */
+  const double *eta;      /* host, length G, each > 0; or NULL: power method */
+  double eta_margin;      /* eta_g = (1+margin) mu Lambda_hat_g; default 0.05 */
+  int32_t power_iters;    /* power-method steps cap; default 100 */
+  double power_tol;       /* power-method relative change stop; default 1e-6 */
+  int32_t precision;      /* FSQR_FP64 | FSQR_MIXED; default FSQR_FP64 */
+  int32_t warm;           /* FSQR_WARM_*; default FSQR_WARM_NONE */
+  int32_t digits;         /* FSQR_MIXED: int8 digits per theta entry, 3..6; default 4 */
+  int32_t max_group;      /* fits advanced together per X pass, 1..8; default 4 */
+  int64_t timeout_ms;     /* > 0: stop with FSQR_ETIMEOUT after this wall time */
+} fsqr_opts;
+
+/* Per-fit report. */
+typedef struct {
+  int32_t status;         /* FSQR_OK, FSQR_ENOCONV, FSQR_ETIMEOUT or FSQR_ENUMERIC */
+  int32_t iters;          /* iteration k of the returned iterate w^k */
+  double kkt, r_p, r_z, r_beta, r_1; /* stop-test residuals of the returned iterate */
+  double primal;          /* (1/n) sum rho_tau(y - X~ beta) + sum lambda_j |beta_j| */
+  double dual, gap;       /* dual value and relative gap (P-D)/(1+|P|+|D|);
+                             NaN when some omega_j = 0 for j >= 1 */
+  double lambda, lambda_max, mu;
+  int64_t active;         /* number of j >= 1 with beta_j != 0 */
+  double t_setup_ms, t_solve_ms;
+} fsqr_info;
+
+/* Version of this ABI (major*10000 + minor*100 + patch). */
+int fsqr_version(void);
+
+/* Fills opts with the defaults listed above. */
+void fsqr_opts_default(fsqr_opts *opts);
+
+/* Creates a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). The context owns its
+ * device workspace, grown on demand and released by fsqr_destroy. */
+int fsqr_create(fsqr_ctx **ctx, int device, void *cuda_stream);
+int fsqr_destroy(fsqr_ctx *ctx);
+/* Last error message of this context ("" if none); valid until the next call. */
+const char *fsqr_last_error(const fsqr_ctx *ctx);
+
+/* Column statistics (row A0 of the hot-path table; Section 7): mean and
+ * population sd over non-missing entries of the c covariates and p feature
+ * columns. mean_out/sd_out: device, length c+p. */
+int fsqr_col_stats(fsqr_ctx *ctx, const fsqr_design *X, double *mean_out, double *sd_out);
+
+/* lambda_max(tau) = max_{j>=1, omega_j>0} |x~_j^T v| / (n omega_j) with
+ * v_i = tau - 1{y_i < y_(ceil(n tau))}: the smallest lambda at which
+ * beta_{1..} = 0 is optimal up to ties (penalty path, Section 7).
+ * y, omega: device (omega length P). out: host scalar. */
+int fsqr_lambda_max(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau,
+                    const double *omega, double *out);
+
+/* Step metric (Section 4): eta_g = (1+margin) mu Lambda_hat(X~_g^T X~_g), with
+ * Lambda_hat from the power method started at v = 1/sqrt(p_g) and stopped
+ * after max_iter steps or a relative change <= tol; a zero block gets
+ * (1+margin) mu. block_ptr: host, G+1 offsets, 0 = block_ptr[0] < ... <
+ * block_ptr[G] = P. eta_out: host, length G. */
+int fsqr_eta(fsqr_ctx *ctx, const fsqr_design *X, const int64_t *block_ptr, int G, double mu,
+             double margin, int max_iter, double tol, double *eta_out);
+
+/* One FS-QRPPA fit (Algorithm 1) at quantile tau in (0,1) and penalty
+ * lambda >= 0, lambda_j = lambda omega_j.
+ *   y: device, length n. omega: device, length P, omega[0] == 0, omega >= 0.
+ *   block_ptr: host, G+1 offsets as for fsqr_eta.
+ *   beta (P), z (n), theta (n): device, in/out. Read as the start when
+ *   opts.warm == FSQR_WARM_GIVEN; on return they hold the iterate that
+ *   passed the stop test (or the last one), beta on the standardised scale.
+ *   info: host, may be NULL.
+ * Returns FSQR_OK, or FSQR_ENOCONV / FSQR_ETIMEOUT with valid outputs. */
+int fsqr_fit(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau, double lambda,
+             const double *omega, const int64_t *block_ptr, int G, const fsqr_opts *opts,
+             double *beta, double *z, double *theta, fsqr_info *info);
+
+/* A tau x lambda grid of fits sharing X, y, omega, the blocks and eta.
+ *   taus: host, n_tau values in (0,1). lambdas: host, n_tau*n_lambda values,
+ *   lambdas[t*n_lambda + l] for tau t (each tau has its own path).
+ *   Fit b = t*n_lambda + l. beta: device, B*P (fit b at beta + b*P);
+ *   z, theta: device, B*n. infos: host, B entries, may be NULL.
+ * With opts.warm == FSQR_WARM_PATH the lambdas of each tau should decrease;
+ * fit (t, l) starts from fit (t, l-1). Returns FSQR_OK if every fit met the
+ * tolerance, else the first non-OK per-fit status. */
+int fsqr_fit_batch(fsqr_ctx *ctx, const fsqr_design *X, const double *y, int n_tau,
+                   const double *taus, int n_lambda, const double *lambdas, const double *omega,
+                   const int64_t *block_ptr, int G, const fsqr_opts *opts, double *beta,
+                   double *z, double *theta, fsqr_info *infos);
+
+/* fsqr_fit_batch from HOST buffers: X->geno, X->cov, X->col_mean/col_sd, y,
+ * omega, beta, z, theta are host pointers. The library copies the inputs to
+ * device workspace, solves, and copies beta/z/theta back; the copies are
+ * part of the call. */
+int fsqr_fit_batch_host(fsqr_ctx *ctx, const fsqr_design *X, const double *y, int n_tau,
+                        const double *taus, int n_lambda, const double *lambdas,
+                        const double *omega, const int64_t *block_ptr, int G,
+                        const fsqr_opts *opts, double *beta, double *z, double *theta,
+                        fsqr_info *infos);
+
+/* Stop-test residuals, primal value and duality gap of a given iterate
+ * (row A8 of the hot-path table). y, omega, beta (P), z, theta (n): device.
+ * lambda_norm > 0 divides R_b. out: host. */
+int fsqr_kkt(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau, double lambda,
+             const double *omega, double lambda_norm, const double *beta, const double *z,
+             const double *theta, fsqr_info *out);
+
+/* Quantile predictions q_tau(x) = x~^T beta (Section 7.1) for B coefficient
+ * vectors: out[b*n + i] = x~_i^T beta_b with beta_b at beta + b*P (device,
+ * standardised scale). For new samples pass the training col_mean/col_sd
+ * in X so that they are standardised the same way. out: device, B*n. */
+int fsqr_predict(fsqr_ctx *ctx, const fsqr_design *X, const double *beta, int B, double *out);
+
+/* Maps B standardised coefficient vectors to the original feature scale
+ * (Section 7): b_j / sd_j for j >= 1 (0 for a constant column) and
+ * b_0 - sum_j mean_j b_j / sd_j. beta_std, beta_out: device, B*P. */
+int fsqr_back_transform(fsqr_ctx *ctx, const fsqr_design *X, const double *beta_std, int B,
+                        double *beta_out);
+
+/* Kernel timing sampled inside the solver (no counterpart in the paper;
+ * used to report the column pass against the memory roofline). When
+ * enabled, every replay of the captured iteration graph records CUDA events
+ * around one launch of each iteration kernel on the context's stream; the
+ * sums and counts accumulate until fsqr_profile_reset. kernel_launches
+ * counts every kernel the library launched (graph replays included). */
+typedef struct {
+  int64_t col_samples;  double col_ms;   /* column pass: X~^T theta + beta prox */
+  int64_t xb_samples;   double xb_ms;    /* X~ beta over the active columns */
+  int64_t vec_samples;  double vec_ms;   /* z, r, theta update */
+  int64_t iterations;                    /* FS-QRPPA steps executed */
+  int64_t kernel_launches;
+  int64_t col_bytes;                     /* algorithmic bytes of the last column pass */
+} fsqr_profile;
+
+int fsqr_profile_enable(fsqr_ctx *ctx, int on);
+int fsqr_profile_get(fsqr_ctx *ctx, fsqr_profile *out);
+int fsqr_profile_reset(fsqr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSQR_H */

@@ -1,0 +1,1146 @@
+// C-ABI layer of the FS-QRPPA library: argument checks, device workspace,
+// setup (column statistics, lambda_max, eta by the power method) and the
+// driver of the inner iteration, which advances groups of up to 8 fits per X
+// pass and replays the iteration as captured CUDA graphs of M steps.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fsqr_internal.h"
+
+using namespace fsqr;
+
+struct fsqr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  std::string err;
+  std::map<std::string, std::pair<void *, size_t>> ws;
+  double *hpin = nullptr;  // pinned host scratch
+  size_t hpin_n = 0;
+  bool prof = false;
+  fsqr_profile pf{};
+  cudaEvent_t ev[6] = {};
+  cudaEvent_t legacy_ev = nullptr;
+};
+
+namespace {
+
+constexpr int kVersion = 10000;
+
+int fail(fsqr_ctx *ctx, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, FSQR_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),        \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+#define TRY(expr)              \
+  do {                         \
+    int rc_ = (expr);          \
+    if (rc_ != FSQR_OK) return rc_; \
+  } while (0)
+
+// Start of every entry point: select the device and, when the library owns
+// its stream, order it after work already queued on the legacy default
+// stream (where callers without an explicit stream put their inputs).
+int enter(fsqr_ctx *ctx) {
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->device));
+  if (ctx->own_stream) {
+    CK(cudaEventRecord(ctx->legacy_ev, cudaStreamLegacy));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->legacy_ev, 0));
+  }
+  return FSQR_OK;
+}
+
+// Named device workspace, grown on demand (contents are not preserved).
+template <class T>
+int wsget(fsqr_ctx *ctx, const char *name, size_t count, T **out) {
+  size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  auto &slot = ctx->ws[name];
+  if (slot.second < bytes) {
+    if (slot.first) cudaFree(slot.first);
+    slot.first = nullptr;
+    slot.second = 0;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, FSQR_ENOMEM, "cudaMalloc(%zu bytes) for %s: %s", bytes, name,
+                  cudaGetErrorString(e));
+    }
+    slot.first = p;
+    slot.second = bytes;
+  }
+  *out = static_cast<T *>(slot.first);
+  return FSQR_OK;
+}
+
+int pinned(fsqr_ctx *ctx, size_t count, double **out) {
+  if (ctx->hpin_n < count) {
+    if (ctx->hpin) cudaFreeHost(ctx->hpin);
+    ctx->hpin = nullptr;
+    ctx->hpin_n = 0;
+    CK(cudaMallocHost(&ctx->hpin, count * sizeof(double)));
+    ctx->hpin_n = count;
+  }
+  *out = ctx->hpin;
+  return FSQR_OK;
+}
+
+int64_t pad16(int64_t n) { return (n + 15) / 16 * 16; }
+
+int64_t col_bytes(int64_t n, int fmt) {
+  if (fmt == FSQR_DENSE_F64) return 8 * n;
+  if (fmt == FSQR_INT8) return n;
+  return (n + 3) / 4;
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int check_design(fsqr_ctx *ctx, const fsqr_design *d) {
+  if (!d) return fail(ctx, FSQR_EINVAL, "design is NULL");
+  if (d->n < 1) return fail(ctx, FSQR_EINVAL, "n must be >= 1 (got %lld)", (long long)d->n);
+  if (d->p < 0 || d->c < 0) return fail(ctx, FSQR_EINVAL, "p and c must be >= 0");
+  if (1 + d->c + d->p > (int64_t)INT32_MAX - 1024)
+    return fail(ctx, FSQR_EINVAL, "too many columns (P = %lld)", (long long)(1 + d->c + d->p));
+  if (d->n > (int64_t)1 << 24) return fail(ctx, FSQR_EINVAL, "n > 2^24 is not supported");
+  if (d->geno_format < FSQR_DENSE_F64 || d->geno_format > FSQR_2BIT)
+    return fail(ctx, FSQR_EINVAL, "unknown geno_format %d", d->geno_format);
+  if (d->standardize != 0 && d->standardize != 1)
+    return fail(ctx, FSQR_EINVAL, "standardize must be 0 or 1");
+  if (d->p > 0) {
+    if (!d->geno) return fail(ctx, FSQR_EINVAL, "geno is NULL with p > 0");
+    if (((uintptr_t)d->geno) % 16) return fail(ctx, FSQR_EINVAL, "geno must be 16-byte aligned");
+    if (d->geno_ld % 16) return fail(ctx, FSQR_EINVAL, "geno_ld must be a multiple of 16");
+    if (d->geno_ld < col_bytes(d->n, d->geno_format))
+      return fail(ctx, FSQR_EINVAL, "geno_ld %lld < %lld bytes needed per column",
+                  (long long)d->geno_ld, (long long)col_bytes(d->n, d->geno_format));
+  }
+  if (d->c > 0 && !d->cov) return fail(ctx, FSQR_EINVAL, "cov is NULL with c > 0");
+  if ((d->col_mean == nullptr) != (d->col_sd == nullptr))
+    return fail(ctx, FSQR_EINVAL, "col_mean and col_sd must be given together");
+  return FSQR_OK;
+}
+
+int check_blocks(fsqr_ctx *ctx, const int64_t *bp, int G, int64_t P) {
+  if (G < 1) return fail(ctx, FSQR_EINVAL, "G must be >= 1");
+  if (!bp) return fail(ctx, FSQR_EINVAL, "block_ptr is NULL");
+  if (bp[0] != 0) return fail(ctx, FSQR_EINVAL, "block_ptr[0] must be 0");
+  for (int g = 0; g < G; ++g)
+    if (bp[g + 1] <= bp[g]) return fail(ctx, FSQR_EINVAL, "block_ptr must be strictly increasing");
+  if (bp[G] != P)
+    return fail(ctx, FSQR_EINVAL, "block_ptr[G] = %lld must equal P = %lld", (long long)bp[G],
+                (long long)P);
+  return FSQR_OK;
+}
+
+// Design prepared for the kernels: affine maps a_j, b_j from the column
+// statistics (given or computed), and the count of missing entries.
+struct Prep {
+  Dsg X;
+  const double *mean = nullptr;  // length c+p
+  const double *sd = nullptr;
+  int missing = 0;
+  double colbound = 0.0;
+};
+
+int prepare(fsqr_ctx *ctx, const fsqr_design *d, Prep *pp, bool need_colbound) {
+  TRY(check_design(ctx, d));
+  Prep &p = *pp;
+  Dsg &X = p.X;
+  X.n = d->n;
+  X.p = d->p;
+  X.c = d->c;
+  X.P = 1 + d->c + d->p;
+  X.fmt = d->geno_format;
+  X.geno = static_cast<const uint8_t *>(d->geno);
+  X.ld = d->geno_ld;
+  X.cov = d->cov;
+  const int64_t F = d->c + d->p;
+  double *mean, *sd, *a, *b;
+  int *miss;
+  TRY(wsget(ctx, "stat_mean", F, &mean));
+  TRY(wsget(ctx, "stat_sd", F, &sd));
+  TRY(wsget(ctx, "aff_a", X.P, &a));
+  TRY(wsget(ctx, "aff_b", X.P, &b));
+  TRY(wsget(ctx, "stat_missing", 1, &miss));
+  CK(cudaMemsetAsync(miss, 0, sizeof(int), ctx->stream));
+  CK(launch_col_stats(X, mean, sd, miss, ctx->stream));
+  p.mean = d->col_mean ? d->col_mean : mean;
+  p.sd = d->col_sd ? d->col_sd : sd;
+  CK(launch_affine(X, p.mean, p.sd, d->standardize, a, b, ctx->stream));
+  X.a = a;
+  X.b = b;
+  int hmiss = 0;
+  CK(cudaMemcpyAsync(&hmiss, miss, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (need_colbound) {
+    double *cb;
+    TRY(wsget(ctx, "colbound", 1, &cb));
+    CK(launch_colbound(X, p.mean, cb, ctx->stream));
+    CK(cudaMemcpyAsync(&p.colbound, cb, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  p.missing = hmiss;
+  if (hmiss > 0)
+    return fail(ctx, FSQR_EINVAL,
+                "%d missing genotype entries: mean imputation of missing entries is not "
+                "supported by this build",
+                hmiss);
+  return FSQR_OK;
+}
+
+// Column-pass tiling: CTA c owns T consecutive columns; T is a multiple of
+// 32 and the grid fits in one wave of resident CTAs when P allows it.
+void col_tiling(fsqr_ctx *ctx, int64_t P, int per_sm, int *gridA, int *T) {
+  const int64_t target = std::max<int64_t>(1, (int64_t)ctx->num_sms * std::max(1, per_sm));
+  int64_t t = (P + target - 1) / target;
+  t = std::max<int64_t>(32, (t + 31) / 32 * 32);
+  *T = (int)t;
+  *gridA = (int)((P + t - 1) / t);
+}
+
+int nb_template(int nb) {
+  if (nb <= 1) return 1;
+  if (nb == 2) return 2;
+  if (nb == 3) return 3;
+  if (nb == 4) return 4;
+  return 8;
+}
+
+// Host-side y statistics: ||y||_inf and population sd.
+int y_stats(fsqr_ctx *ctx, const double *y, int64_t n, double *ymax, double *ysd) {
+  double *st;
+  TRY(wsget(ctx, "ystats", 3, &st));
+  CK(launch_vec_stats(y, n, st, ctx->stream));
+  double h[3];
+  CK(cudaMemcpyAsync(h, st, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const double m = h[0] / (double)n;
+  double v = h[1] / (double)n - m * m;
+  *ymax = h[2];
+  *ysd = sqrt(v > 0 ? v : 0.0);
+  if (!(h[0] == h[0]) || !(h[1] == h[1]) || isinf(h[1]))
+    return fail(ctx, FSQR_ENUMERIC, "y contains NaN or Inf");
+  return FSQR_OK;
+}
+
+// A Fits with only the column tiling set, for the non-iteration passes.
+Fits pass_fits(fsqr_ctx *ctx, const Dsg &X) {
+  Fits F{};
+  F.n = X.n;
+  F.npad = pad16(X.n);
+  col_tiling(ctx, X.P, 4, &F.gridA, &F.T);
+  return F;
+}
+
+// lambda_max(tau) for one tau (host result).
+int lambda_max_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, const double *omega,
+                    double *out) {
+  const Dsg &X = pr.X;
+  const int64_t n = X.n, npad = pad16(n);
+  double *q, *v, *vs, *s, *o;
+  TRY(wsget(ctx, "lmax_q", 1, &q));
+  TRY(wsget(ctx, "lmax_v", npad, &v));
+  TRY(wsget(ctx, "lmax_vs", 1, &vs));
+  TRY(wsget(ctx, "lmax_s", X.P, &s));
+  TRY(wsget(ctx, "lmax_o", 1, &o));
+  int64_t k = (int64_t)ceil((double)n * tau);
+  if (k < 1) k = 1;
+  if (k > n) k = n;
+  CK(launch_select(y, n, k, q, ctx->stream));
+  CK(launch_lmax_vec(y, n, npad, tau, q, v, ctx->stream));
+  CK(launch_sum_cols(v, n, npad, 1, vs, nullptr, ctx->stream));
+  Fits F = pass_fits(ctx, X);
+  CK(launch_col_pass(A_XT, 1, X, F, 0, v, vs, s, nullptr, ctx->stream));
+  CK(launch_colmax_ratio(s, omega, X.P, (double)n, o, ctx->stream));
+  CK(cudaMemcpyAsync(out, o, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSQR_OK;
+}
+
+// eta_g = (1 + margin) mu Lambda_hat_g by the batched power method.
+int eta_impl(fsqr_ctx *ctx, const Prep &pr, const int64_t *bp, int G, double mu, double margin,
+             int max_iter, double tol, double *eta_out) {
+  const Dsg &X = pr.X;
+  const int64_t n = X.n, npad = pad16(n), P = X.P;
+  // split table: ranges of at most C columns inside one block
+  const int64_t C = std::max<int64_t>(256, (P + 1023) / 1024);
+  std::vector<int64_t> splits;
+  std::vector<int> sob(G + 1, 0);
+  for (int g = 0; g < G; ++g) {
+    sob[g] = (int)(splits.size() / 2);
+    for (int64_t j = bp[g]; j < bp[g + 1]; j += C) {
+      splits.push_back(j);
+      splits.push_back(std::min(bp[g + 1], j + C));
+    }
+  }
+  sob[G] = (int)(splits.size() / 2);
+  const int nsplit = sob[G];
+  int64_t *d_splits, *d_bp;
+  int *d_sob;
+  double *v, *U, *part, *usum, *usq, *w, *wn;
+  TRY(wsget(ctx, "pw_splits", splits.size(), &d_splits));
+  TRY(wsget(ctx, "pw_sob", (size_t)G + 1, &d_sob));
+  TRY(wsget(ctx, "pw_bp", (size_t)G + 1, &d_bp));
+  TRY(wsget(ctx, "pw_v", P, &v));
+  TRY(wsget(ctx, "pw_U", (size_t)G * npad, &U));
+  TRY(wsget(ctx, "pw_part", (size_t)nsplit * npad, &part));
+  TRY(wsget(ctx, "pw_usum", G, &usum));
+  TRY(wsget(ctx, "pw_usq", G, &usq));
+  TRY(wsget(ctx, "pw_w", P, &w));
+  TRY(wsget(ctx, "pw_wn", G, &wn));
+  CK(cudaMemcpyAsync(d_splits, splits.data(), splits.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(d_sob, sob.data(), sob.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(d_bp, bp, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(launch_power_init(v, d_bp, G, P, ctx->stream));
+  Fits F = pass_fits(ctx, X);
+  F.block_ptr = d_bp;
+  F.G = G;
+  std::vector<double> lam(G, 0.0), res(G, 0.0), hq(G), hw(G);
+  std::vector<char> frozen(G, 0);
+  int left = G;
+  for (int t = 1; t <= max_iter && left > 0; ++t) {
+    CK(launch_xv_blocks(X, v, d_splits, d_sob, G, nsplit, U, npad, part, ctx->stream));
+    CK(launch_sum_cols(U, n, npad, G, usum, usq, ctx->stream));
+    CK(launch_col_pass(A_XT_BLOCK, 1, X, F, 0, U, usum, w, nullptr, ctx->stream));
+    CK(launch_power_step(w, d_bp, G, P, v, wn, ctx->stream));
+    CK(cudaMemcpyAsync(hq.data(), usq, G * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hw.data(), wn, G * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int g = 0; g < G; ++g) {
+      if (frozen[g]) continue;
+      if (hw[g] == 0.0) {
+        res[g] = 0.0;
+        frozen[g] = 1;
+        --left;
+      } else if (fabs(hq[g] - lam[g]) <= tol * hq[g]) {
+        res[g] = hq[g];
+        frozen[g] = 1;
+        --left;
+      } else {
+        lam[g] = hq[g];
+      }
+    }
+  }
+  for (int g = 0; g < G; ++g) {
+    const double L = frozen[g] ? res[g] : lam[g];
+    eta_out[g] = (1.0 + margin) * mu * (L > 0.0 ? L : 1.0);
+  }
+  return FSQR_OK;
+}
+
+int check_opts(fsqr_ctx *ctx, const fsqr_opts *o, int G) {
+  if (!o) return fail(ctx, FSQR_EINVAL, "opts is NULL");
+  if (!(o->tol >= 0.0)) return fail(ctx, FSQR_EINVAL, "tol must be >= 0");
+  if (o->max_iter < 0) return fail(ctx, FSQR_EINVAL, "max_iter must be >= 0");
+  if (o->check_every < 1) return fail(ctx, FSQR_EINVAL, "check_every must be >= 1");
+  if (o->precision != FSQR_FP64 && o->precision != FSQR_MIXED)
+    return fail(ctx, FSQR_EINVAL, "unknown precision %d", o->precision);
+  if (o->warm < FSQR_WARM_NONE || o->warm > FSQR_WARM_PATH)
+    return fail(ctx, FSQR_EINVAL, "unknown warm mode %d", o->warm);
+  if (o->precision == FSQR_MIXED && (o->digits < 3 || o->digits > 5))
+    return fail(ctx, FSQR_EINVAL, "digits must be in 3..5");
+  if (o->max_group < 1 || o->max_group > kMaxNB)
+    return fail(ctx, FSQR_EINVAL, "max_group must be in 1..8");
+  if (o->eta)
+    for (int g = 0; g < G; ++g)
+      if (!(o->eta[g] > 0.0) || isinf(o->eta[g]))
+        return fail(ctx, FSQR_EINVAL, "eta[%d] must be finite and > 0", g);
+  if (!(o->eta_margin >= 0.0)) return fail(ctx, FSQR_EINVAL, "eta_margin must be >= 0");
+  return FSQR_OK;
+}
+
+// One group of nb fits advanced together to convergence.
+struct GroupSpec {
+  int nb;
+  double tau[kMaxNB], lam[kMaxNB], lamnorm[kMaxNB];
+  int fit[kMaxNB];          // output fit index of each slot
+  int src_fit[kMaxNB];      // start: fit index to read beta/z/theta from (-1 = cold)
+};
+
+struct SolveEnv {
+  const Prep *pr;
+  const double *y;
+  const double *omega;
+  int64_t *d_bp;
+  int G;
+  double *d_eta, *d_ieta;
+  double mu, ymax;
+  bool gap_defined;
+  const fsqr_opts *o;
+  double *beta, *z, *theta;  // user arrays (fit-major)
+  fsqr_info *infos;
+  double deadline_ms;        // <= 0: none
+};
+
+int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
+  const Dsg &X = E.pr->X;
+  const int nb = gs.nb;
+  const int NB = nb_template(nb);
+  const int64_t n = X.n, npad = pad16(n), P = X.P;
+  const bool mixed = E.o->precision == FSQR_MIXED;
+  const double t0 = now_ms();
+  cudaStream_t st = ctx->stream;
+
+  Fits F{};
+  F.nb = nb;
+  F.n = n;
+  F.npad = npad;
+  F.y = E.y;
+  F.ymax = E.ymax;
+  F.omega = E.omega;
+  F.block_ptr = E.d_bp;
+  F.G = E.G;
+  F.eta = E.d_eta;
+  F.inv_eta = E.d_ieta;
+  for (int b = 0; b < kMaxNB; ++b) {
+    F.tau[b] = b < nb ? gs.tau[b] : 0.5;
+    F.lam[b] = b < nb ? gs.lam[b] : 0.0;
+    F.lamnorm[b] = b < nb ? gs.lamnorm[b] : 1.0;
+  }
+  F.mu = E.mu;
+  F.sigma = E.mu / (double)(E.G + 1);
+  F.tol = E.o->tol;
+  F.K = E.o->check_every;
+  F.max_iter = E.o->max_iter;
+  F.mixed = mixed ? 1 : 0;
+  F.D = mixed ? E.o->digits : 0;
+  F.n4p = npad / 4;
+  F.colbound = E.pr->colbound;
+  // tiling from the occupancy of the kernel this group runs
+  {
+    Fits tmp = F;
+    tmp.T = 32;
+    size_t smem_est = col_pass_smem(A_PROX, tmp, NB) + 4096;
+    int per_sm = col_pass_occupancy(NB, F.mixed, F.D, smem_est);
+    if (per_sm < 1)
+      return fail(ctx, FSQR_EINVAL, "group of %d fits does not fit on an SM (shared memory %zu B)",
+                  nb, smem_est);
+    col_tiling(ctx, P, per_sm, &F.gridA, &F.T);
+  }
+  F.gridC = (int)((n * NB + kCThreads - 1) / kCThreads);
+  TRY(wsget(ctx, "g_beta0", (size_t)P * NB, &F.beta[0]));
+  TRY(wsget(ctx, "g_beta1", (size_t)P * NB, &F.beta[1]));
+  TRY(wsget(ctx, "g_z", (size_t)npad * NB, &F.z));
+  TRY(wsget(ctx, "g_theta", (size_t)npad * NB, &F.theta));
+  TRY(wsget(ctx, "g_r", (size_t)npad * NB, &F.r));
+  TRY(wsget(ctx, "g_arb", (size_t)F.gridA * NB, &F.a_rb));
+  TRY(wsget(ctx, "g_act", (size_t)F.gridA * NB, &F.a_ct));
+  TRY(wsget(ctx, "g_acnt", (size_t)F.gridA, &F.a_cnt));
+  TRY(wsget(ctx, "g_alist", (size_t)F.gridA * F.T, &F.a_list));
+  TRY(wsget(ctx, "g_xbpart", (size_t)kBMaxSplits * npad * NB, &F.xb_part));
+  TRY(wsget(ctx, "g_metai", 4, &F.meta_i));
+  TRY(wsget(ctx, "g_metad", kMaxNB, &F.meta_d));
+  TRY(wsget(ctx, "g_cpart0", (size_t)F.gridC * NB * kCPartials, &F.c_part[0]));
+  TRY(wsget(ctx, "g_cpart1", (size_t)F.gridC * NB * kCPartials, &F.c_part[1]));
+  TRY(wsget(ctx, "g_done", kMaxNB, &F.done));
+  TRY(wsget(ctx, "g_ndone", 1, &F.n_done));
+  TRY(wsget(ctx, "g_report", (size_t)kMaxNB * kReport, &F.report));
+  int *it_base;
+  TRY(wsget(ctx, "g_itbase", 1, &it_base));
+  F.it_base = it_base;
+  if (mixed) {
+    TRY(wsget(ctx, "g_digits", (size_t)NB * F.D * F.n4p, &F.digits));
+    TRY(wsget(ctx, "g_scale", kMaxNB, &F.scale));
+  }
+  const size_t smem = col_pass_smem(A_PROX, F, NB);
+  if (smem > 227 * 1024)
+    return fail(ctx, FSQR_EINVAL, "mixed group needs %zu B of shared memory (> 227 KB)", smem);
+
+  // ---- start point
+  CK(cudaMemsetAsync(F.report, 0, sizeof(double) * kMaxNB * kReport, st));
+  CK(cudaMemsetAsync(F.z, 0, sizeof(double) * npad * NB, st));
+  CK(cudaMemsetAsync(F.theta, 0, sizeof(double) * npad * NB, st));
+  CK(cudaMemsetAsync(F.r, 0, sizeof(double) * npad * NB, st));
+  CK(cudaMemsetAsync(F.beta[0], 0, sizeof(double) * P * NB, st));
+  CK(cudaMemsetAsync(F.beta[1], 0, sizeof(double) * P * NB, st));
+  bool cold = true;
+  for (int b = 0; b < nb; ++b) cold = cold && gs.src_fit[b] < 0;
+  CK(launch_init_state(NB, F, nb, cold ? FSQR_WARM_NONE : FSQR_WARM_GIVEN, st));
+  if (!cold) {
+    // per slot: warm slots copy from the user's arrays, cold ones take y
+    for (int b = 0; b < nb; ++b) {
+      const int sf = gs.src_fit[b];
+      if (sf >= 0) {
+        CK(launch_pack(E.beta + (int64_t)sf * P, P, F.beta[0] + b, P, 1, NB, P, st));
+        CK(launch_pack(E.z + (int64_t)sf * n, n, F.z + b, n, 1, NB, npad, st));
+        CK(launch_pack(E.theta + (int64_t)sf * n, n, F.theta + b, n, 1, NB, npad, st));
+      } else {
+        CK(launch_pack(E.y, n, F.z + b, n, 1, NB, npad, st));
+      }
+    }
+  }
+  CK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, F.beta[0], st));
+  CK(launch_xbeta(NB, X, F, 0, F.beta[0], st));
+  CK(launch_vec(NB, F, 0, 1, st));
+
+  // ---- the iteration as a captured graph of M steps
+  const int K = F.K;
+  const int M = K * std::max(1, (20 + K - 1) / K);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const bool prof = ctx->prof;
+  if (prof && !ctx->ev[0])
+    for (int e = 0; e < 6; ++e) CK(cudaEventCreate(&ctx->ev[e]));
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = cudaSuccess;
+  int per_graph = 1;  // the advance kernel
+  for (int off = 0; off < M && ce == cudaSuccess; ++off) {
+    const bool sample = prof && off == 1;
+    if (mixed && ce == cudaSuccess) ce = launch_quantize(NB, F, off, st);
+    if (sample && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[0], st);
+    if (ce == cudaSuccess) ce = launch_col_pass(A_PROX, NB, X, F, off, nullptr, nullptr, nullptr, nullptr, st);
+    if (sample && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[1], st);
+    if (ce == cudaSuccess) ce = launch_xbeta(NB, X, F, off, nullptr, st);
+    if (sample && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], st);
+    if (off % K == 0 && ce == cudaSuccess) ce = launch_check(NB, F, off, st);
+    if (sample && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[3], st);
+    if (ce == cudaSuccess) ce = launch_vec(NB, F, off, 0, st);
+    if (sample && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[4], st);
+    per_graph += 3 + (mixed ? 1 : 0) + (off % K == 0 ? 1 : 0);
+  }
+  if (ce == cudaSuccess) ce = launch_advance(it_base, M, st);
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (ce != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return fail(ctx, FSQR_ECUDA, "graph capture failed: %s",
+                cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+  }
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return fail(ctx, FSQR_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+
+  double *hp;
+  TRY(pinned(ctx, 64, &hp));
+  int *hdone = reinterpret_cast<int *>(hp);
+  const int64_t max_launch = (int64_t)E.o->max_iter / M + 3;
+  bool timed_out = false;
+  int host_base = 0;
+  int rc = FSQR_OK;
+  for (int64_t l = 0;; ++l) {
+    ce = cudaGraphLaunch(exec, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hdone, F.n_done, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+      rc = fail(ctx, FSQR_ECUDA, "iteration graph: %s", cudaGetErrorString(ce));
+      break;
+    }
+    host_base += M;
+    ctx->pf.kernel_launches += per_graph;
+    if (prof) {
+      float a = 0.f, b = 0.f, c = 0.f;
+      if (cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]) == cudaSuccess &&
+          cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]) == cudaSuccess &&
+          cudaEventElapsedTime(&c, ctx->ev[3], ctx->ev[4]) == cudaSuccess) {
+        ctx->pf.col_ms += a;
+        ctx->pf.col_samples += 1;
+        ctx->pf.xb_ms += b;
+        ctx->pf.xb_samples += 1;
+        ctx->pf.vec_ms += c;
+        ctx->pf.vec_samples += 1;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    if (*hdone >= nb) break;
+    if (E.deadline_ms > 0 && now_ms() > E.deadline_ms) {
+      timed_out = true;
+      break;
+    }
+    if (l > max_launch) {
+      rc = fail(ctx, FSQR_ECUDA, "iteration did not stop after %d steps", host_base);
+      break;
+    }
+  }
+  cudaGraphExecDestroy(exec);
+  if (rc != FSQR_OK) return rc;
+  {
+    // iterations actually taken by the live fits (done fits idle afterwards)
+    int hd0[kMaxNB];
+    CK(cudaMemcpyAsync(hd0, F.done, sizeof(int) * NB, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int kmax = 0;
+    for (int b = 0; b < nb; ++b) kmax = std::max(kmax, hd0[b] >= 0 ? hd0[b] : host_base);
+    ctx->pf.iterations += kmax;
+    // algorithmic bytes of one column pass: the stored X, the covariates,
+    // beta^k read and beta^{k+1} written for the NB interleaved fits
+    const int64_t xbytes = (X.fmt == FSQR_DENSE_F64 ? 8 * n : X.fmt == FSQR_INT8 ? n : (n + 3) / 4) * X.p;
+    ctx->pf.col_bytes = xbytes + 8 * n * X.c + 2 * 8 * P * NB;
+  }
+
+  // ---- results
+  int hd[kMaxNB];
+  double rep[kMaxNB * kReport];
+  CK(cudaMemcpyAsync(hd, F.done, sizeof(int) * NB, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rep, F.report, sizeof(double) * NB * kReport, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int b = 0; b < nb; ++b) {
+    const int k_fin = (hd[b] >= 0) ? hd[b] : host_base;
+    const int f = gs.fit[b];
+    CK(launch_unpack(F.beta[k_fin & 1] + b, E.beta + (int64_t)f * P, P, P, 1, NB, st));
+    CK(launch_unpack(F.z + b, E.z + (int64_t)f * n, n, n, 1, NB, st));
+    CK(launch_unpack(F.theta + b, E.theta + (int64_t)f * n, n, n, 1, NB, st));
+  }
+  const double t_solve = now_ms() - t0;
+
+  if (E.infos) {
+    // primal value, active count and duality gap of each returned iterate
+    double *bfin, *tc, *tcs, *schk, *summ, *dtaus, *dlams;
+    TRY(wsget(ctx, "r_bfin", (size_t)P * NB, &bfin));
+    TRY(wsget(ctx, "r_tc", (size_t)npad * NB, &tc));
+    TRY(wsget(ctx, "r_tcs", kMaxNB, &tcs));
+    TRY(wsget(ctx, "r_schk", (size_t)P * NB, &schk));
+    TRY(wsget(ctx, "r_summ", (size_t)kMaxNB * 8, &summ));
+    TRY(wsget(ctx, "r_taus", kMaxNB, &dtaus));
+    TRY(wsget(ctx, "r_lams", kMaxNB, &dlams));
+    CK(cudaMemsetAsync(bfin, 0, sizeof(double) * P * NB, st));
+    for (int b = 0; b < nb; ++b)
+      CK(launch_pack(E.beta + (int64_t)gs.fit[b] * P, P, bfin + b, P, 1, NB, P, st));
+    CK(cudaMemcpyAsync(dtaus, F.tau, sizeof(double) * kMaxNB, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dlams, F.lam, sizeof(double) * kMaxNB, cudaMemcpyHostToDevice, st));
+    const double *schk_use = nullptr, *tc_use = nullptr;
+    if (E.gap_defined) {
+      CK(launch_dual_point(NB, F.theta, n, npad, dtaus, nb, tc, tcs, st));
+      Fits Fx = F;
+      CK(launch_col_pass(A_XT, NB, X, Fx, 0, tc, tcs, schk, nullptr, st));
+      schk_use = schk;
+      tc_use = tc;
+    }
+    CK(launch_summary(NB, nb, n, P, E.y, F.z, F.r, bfin, E.omega, dtaus, dlams, schk_use, tc_use,
+                      summ, st));
+    double hs[kMaxNB * 8];
+    CK(cudaMemcpyAsync(hs, summ, sizeof(double) * kMaxNB * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int b = 0; b < nb; ++b) {
+      fsqr_info &I = E.infos[gs.fit[b]];
+      const double *rp = rep + b * kReport;
+      I.status = timed_out && hd[b] < 0 ? FSQR_ETIMEOUT : (int)rp[5];
+      I.iters = hd[b] >= 0 ? hd[b] : host_base;
+      I.kkt = rp[0];
+      I.r_p = rp[1];
+      I.r_z = rp[2];
+      I.r_beta = rp[3];
+      I.r_1 = rp[4];
+      I.primal = hs[b * 8 + 0] + hs[b * 8 + 1];
+      I.active = (int64_t)hs[b * 8 + 2];
+      if (E.gap_defined) {
+        I.dual = hs[b * 8 + 3] * hs[b * 8 + 4];
+        I.gap = (I.primal - I.dual) / (1.0 + fabs(I.primal) + fabs(I.dual));
+      } else {
+        I.dual = NAN;
+        I.gap = NAN;
+      }
+      I.lambda = gs.lam[b];
+      I.lambda_max = gs.lamnorm[b];
+      I.mu = E.mu;
+      I.t_solve_ms = t_solve;
+    }
+  } else {
+    CK(cudaStreamSynchronize(st));
+  }
+  return timed_out ? FSQR_ETIMEOUT : FSQR_OK;
+}
+
+int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_tau,
+                   const double *taus, int n_lambda, const double *lambdas, const double *omega,
+                   const int64_t *block_ptr, int G, const fsqr_opts *opts, double *beta, double *z,
+                   double *theta, fsqr_info *infos) {
+  const double t0 = now_ms();
+  TRY(check_opts(ctx, opts, G));
+  if (n_tau < 1 || n_lambda < 1) return fail(ctx, FSQR_EINVAL, "n_tau and n_lambda must be >= 1");
+  if (!taus || !lambdas) return fail(ctx, FSQR_EINVAL, "taus/lambdas are NULL");
+  if (!y || !omega || !beta || !z || !theta) return fail(ctx, FSQR_EINVAL, "NULL array argument");
+  for (int t = 0; t < n_tau; ++t)
+    if (!(taus[t] > 0.0 && taus[t] < 1.0)) return fail(ctx, FSQR_EINVAL, "tau must be in (0,1)");
+  for (int t = 0; t < n_tau * n_lambda; ++t)
+    if (!(lambdas[t] >= 0.0) || isinf(lambdas[t]))
+      return fail(ctx, FSQR_EINVAL, "lambda must be finite and >= 0");
+  if (opts->precision == FSQR_MIXED && Xd && Xd->geno_format != FSQR_INT8)
+    return fail(ctx, FSQR_EINVAL, "FSQR_MIXED needs FSQR_INT8 genotype storage");
+  Prep pr;
+  TRY(prepare(ctx, Xd, &pr, opts->precision == FSQR_MIXED));
+  const Dsg &X = pr.X;
+  const int64_t P = X.P, n = X.n;
+  TRY(check_blocks(ctx, block_ptr, G, P));
+  // omega: omega[0] == 0, omega >= 0; gap defined iff omega_j > 0 for j >= 1
+  double om[2];
+  {
+    double *d;
+    TRY(wsget(ctx, "omega_chk", 2, &d));
+    CK(cudaMemcpyAsync(d, omega, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(launch_min_omega(omega, P, d + 1, ctx->stream));
+    CK(cudaMemcpyAsync(om, d, sizeof om, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (om[0] != 0.0) return fail(ctx, FSQR_EINVAL, "omega[0] must be 0 (intercept unpenalised)");
+  if (P > 1 && !(om[1] >= 0.0)) return fail(ctx, FSQR_EINVAL, "omega must be >= 0");
+  double ymax, ysd;
+  TRY(y_stats(ctx, y, n, &ymax, &ysd));
+  const double mu = opts->mu > 0.0 ? opts->mu : 1.0 / ((double)n * (ysd > 0.0 ? ysd : 1.0));
+  std::vector<double> eta(G);
+  if (opts->eta) {
+    for (int g = 0; g < G; ++g) eta[g] = opts->eta[g];
+  } else {
+    TRY(eta_impl(ctx, pr, block_ptr, G, mu, opts->eta_margin, opts->power_iters, opts->power_tol,
+                 eta.data()));
+  }
+  std::vector<double> lmax(n_tau);
+  for (int t = 0; t < n_tau; ++t) TRY(lambda_max_impl(ctx, pr, y, taus[t], omega, &lmax[t]));
+
+  SolveEnv E{};
+  E.pr = &pr;
+  E.y = y;
+  E.omega = omega;
+  E.G = G;
+  E.mu = mu;
+  E.ymax = ymax;
+  E.gap_defined = (P == 1) || (om[1] > 0.0);
+  E.o = opts;
+  E.beta = beta;
+  E.z = z;
+  E.theta = theta;
+  E.infos = infos;
+  E.deadline_ms = opts->timeout_ms > 0 ? t0 + (double)opts->timeout_ms : 0.0;
+  TRY(wsget(ctx, "eta", G, &E.d_eta));
+  TRY(wsget(ctx, "ieta", G, &E.d_ieta));
+  TRY(wsget(ctx, "bp", (size_t)G + 1, &E.d_bp));
+  std::vector<double> ieta(G);
+  for (int g = 0; g < G; ++g) ieta[g] = 1.0 / eta[g];
+  CK(cudaMemcpyAsync(E.d_eta, eta.data(), G * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(E.d_ieta, ieta.data(), G * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(E.d_bp, block_ptr, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+  const double t_setup = now_ms() - t0;
+
+  // groups of fits
+  const int B = n_tau * n_lambda;
+  const int mg = opts->max_group;
+  std::vector<GroupSpec> groups;
+  if (opts->warm == FSQR_WARM_PATH) {
+    for (int l = 0; l < n_lambda; ++l)
+      for (int t0g = 0; t0g < n_tau; t0g += mg) {
+        GroupSpec gs{};
+        gs.nb = std::min(mg, n_tau - t0g);
+        for (int q = 0; q < gs.nb; ++q) {
+          const int t = t0g + q, f = t * n_lambda + l;
+          gs.tau[q] = taus[t];
+          gs.lam[q] = lambdas[f];
+          gs.lamnorm[q] = lmax[t] > 0.0 ? lmax[t] : 1.0;
+          gs.fit[q] = f;
+          gs.src_fit[q] = (l == 0) ? -1 : f - 1;
+        }
+        groups.push_back(gs);
+      }
+  } else {
+    for (int f0 = 0; f0 < B; f0 += mg) {
+      GroupSpec gs{};
+      gs.nb = std::min(mg, B - f0);
+      for (int q = 0; q < gs.nb; ++q) {
+        const int f = f0 + q, t = f / n_lambda;
+        gs.tau[q] = taus[t];
+        gs.lam[q] = lambdas[f];
+        gs.lamnorm[q] = lmax[t] > 0.0 ? lmax[t] : 1.0;
+        gs.fit[q] = f;
+        gs.src_fit[q] = (opts->warm == FSQR_WARM_GIVEN) ? f : -1;
+      }
+      groups.push_back(gs);
+    }
+  }
+  int worst = FSQR_OK;
+  for (const GroupSpec &gs : groups) {
+    int rc = solve_group(ctx, E, gs);
+    if (rc != FSQR_OK && rc != FSQR_ETIMEOUT) return rc;
+    if (rc == FSQR_ETIMEOUT) E.deadline_ms = 1.0;  // later groups stop right away
+  }
+  if (infos)
+    for (int f = 0; f < B; ++f) {
+      infos[f].t_setup_ms = t_setup;
+      if (worst == FSQR_OK && infos[f].status != FSQR_OK) worst = infos[f].status;
+    }
+  return worst;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+
+extern "C" {
+
+int fsqr_version(void) { return kVersion; }
+
+void fsqr_opts_default(fsqr_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->tol = 1e-6;
+  o->max_iter = 100000;
+  o->check_every = 10;
+  o->mu = 0.0;
+  o->eta = nullptr;
+  o->eta_margin = 0.05;
+  o->power_iters = 100;
+  o->power_tol = 1e-6;
+  o->precision = FSQR_FP64;
+  o->warm = FSQR_WARM_NONE;
+  o->digits = 4;
+  o->max_group = 4;
+  o->timeout_ms = 0;
+}
+
+int fsqr_create(fsqr_ctx **out, int device, void *cuda_stream) {
+  if (!out) return FSQR_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return FSQR_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return FSQR_ECUDA;
+  fsqr_ctx *ctx = new fsqr_ctx();
+  ctx->device = device;
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return FSQR_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (cudaEventCreateWithFlags(&ctx->legacy_ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return FSQR_ECUDA;
+  }
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (ctx->num_sms <= 0) ctx->num_sms = 1;
+  *out = ctx;
+  return FSQR_OK;
+}
+
+int fsqr_destroy(fsqr_ctx *ctx) {
+  if (!ctx) return FSQR_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &kv : ctx->ws)
+    if (kv.second.first) cudaFree(kv.second.first);
+  if (ctx->hpin) cudaFreeHost(ctx->hpin);
+  for (int e = 0; e < 6; ++e)
+    if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
+  if (ctx->legacy_ev) cudaEventDestroy(ctx->legacy_ev);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return FSQR_OK;
+}
+
+const char *fsqr_last_error(const fsqr_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int fsqr_col_stats(fsqr_ctx *ctx, const fsqr_design *X, double *mean_out, double *sd_out) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!mean_out || !sd_out) return fail(ctx, FSQR_EINVAL, "NULL output");
+  Prep pr;
+  TRY(prepare(ctx, X, &pr, false));
+  const int64_t F = X->c + X->p;
+  if (F > 0) {
+    CK(cudaMemcpyAsync(mean_out, pr.mean, F * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(sd_out, pr.sd, F * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSQR_OK;
+}
+
+int fsqr_lambda_max(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau,
+                    const double *omega, double *out) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!y || !omega || !out) return fail(ctx, FSQR_EINVAL, "NULL argument");
+  if (!(tau > 0.0 && tau < 1.0)) return fail(ctx, FSQR_EINVAL, "tau must be in (0,1)");
+  Prep pr;
+  TRY(prepare(ctx, X, &pr, false));
+  return lambda_max_impl(ctx, pr, y, tau, omega, out);
+}
+
+int fsqr_eta(fsqr_ctx *ctx, const fsqr_design *X, const int64_t *block_ptr, int G, double mu,
+             double margin, int max_iter, double tol, double *eta_out) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!eta_out) return fail(ctx, FSQR_EINVAL, "NULL output");
+  if (!(mu > 0.0)) return fail(ctx, FSQR_EINVAL, "mu must be > 0");
+  if (!(margin >= 0.0) || max_iter < 1 || !(tol >= 0.0))
+    return fail(ctx, FSQR_EINVAL, "bad margin/max_iter/tol");
+  Prep pr;
+  TRY(prepare(ctx, X, &pr, false));
+  TRY(check_blocks(ctx, block_ptr, G, pr.X.P));
+  return eta_impl(ctx, pr, block_ptr, G, mu, margin, max_iter, tol, eta_out);
+}
+
+int fsqr_fit_batch(fsqr_ctx *ctx, const fsqr_design *X, const double *y, int n_tau,
+                   const double *taus, int n_lambda, const double *lambdas, const double *omega,
+                   const int64_t *block_ptr, int G, const fsqr_opts *opts, double *beta, double *z,
+                   double *theta, fsqr_info *infos) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  std::vector<fsqr_info> local;
+  if (!infos) {
+    local.resize((size_t)std::max(1, n_tau * n_lambda));
+    infos = local.data();
+  }
+  memset(infos, 0, sizeof(fsqr_info) * (size_t)std::max(0, n_tau * n_lambda));
+  return fit_batch_impl(ctx, X, y, n_tau, taus, n_lambda, lambdas, omega, block_ptr, G, opts,
+                        beta, z, theta, infos);
+}
+
+int fsqr_fit(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau, double lambda,
+             const double *omega, const int64_t *block_ptr, int G, const fsqr_opts *opts,
+             double *beta, double *z, double *theta, fsqr_info *info) {
+  if (!ctx) return FSQR_EINVAL;
+  if (opts && opts->warm == FSQR_WARM_PATH)
+    return fail(ctx, FSQR_EINVAL, "FSQR_WARM_PATH applies to fsqr_fit_batch only");
+  fsqr_info tmp;
+  return fsqr_fit_batch(ctx, X, y, 1, &tau, 1, &lambda, omega, block_ptr, G, opts, beta, z, theta,
+                        info ? info : &tmp);
+}
+
+int fsqr_fit_batch_host(fsqr_ctx *ctx, const fsqr_design *X, const double *y, int n_tau,
+                        const double *taus, int n_lambda, const double *lambdas,
+                        const double *omega, const int64_t *block_ptr, int G,
+                        const fsqr_opts *opts, double *beta, double *z, double *theta,
+                        fsqr_info *infos) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  TRY(check_design(ctx, X));
+  if (!y || !omega || !beta || !z || !theta || n_tau < 1 || n_lambda < 1)
+    return fail(ctx, FSQR_EINVAL, "NULL array argument or empty grid");
+  const int64_t n = X->n, P = 1 + X->c + X->p, F = X->c + X->p;
+  const int64_t B = (int64_t)n_tau * n_lambda;
+  cudaStream_t st = ctx->stream;
+  fsqr_design D = *X;
+  uint8_t *dg = nullptr;
+  double *dc = nullptr, *dm = nullptr, *ds = nullptr, *dy, *dom, *db, *dz, *dt;
+  if (X->p > 0) {
+    TRY(wsget(ctx, "h_geno", (size_t)(X->p * X->geno_ld), &dg));
+    CK(cudaMemcpyAsync(dg, X->geno, (size_t)(X->p * X->geno_ld), cudaMemcpyHostToDevice, st));
+  }
+  if (X->c > 0) {
+    TRY(wsget(ctx, "h_cov", (size_t)(X->c * n), &dc));
+    CK(cudaMemcpyAsync(dc, X->cov, (size_t)(X->c * n) * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  if (X->col_mean) {
+    TRY(wsget(ctx, "h_mean", (size_t)F, &dm));
+    TRY(wsget(ctx, "h_sd", (size_t)F, &ds));
+    CK(cudaMemcpyAsync(dm, X->col_mean, F * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ds, X->col_sd, F * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  TRY(wsget(ctx, "h_y", (size_t)n, &dy));
+  TRY(wsget(ctx, "h_omega", (size_t)P, &dom));
+  TRY(wsget(ctx, "h_beta", (size_t)(B * P), &db));
+  TRY(wsget(ctx, "h_z", (size_t)(B * n), &dz));
+  TRY(wsget(ctx, "h_theta", (size_t)(B * n), &dt));
+  CK(cudaMemcpyAsync(dy, y, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dom, omega, P * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (opts && opts->warm == FSQR_WARM_GIVEN) {
+    CK(cudaMemcpyAsync(db, beta, B * P * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dz, z, B * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dt, theta, B * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  D.geno = dg;
+  D.cov = dc;
+  D.col_mean = dm;
+  D.col_sd = ds;
+  int rc = fsqr_fit_batch(ctx, &D, dy, n_tau, taus, n_lambda, lambdas, dom, block_ptr, G, opts, db,
+                          dz, dt, infos);
+  if (rc != FSQR_OK && rc != FSQR_ENOCONV && rc != FSQR_ETIMEOUT) return rc;
+  CK(cudaMemcpyAsync(beta, db, B * P * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(z, dz, B * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(theta, dt, B * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return rc;
+}
+
+int fsqr_kkt(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, double tau, double lambda,
+             const double *omega, double lambda_norm, const double *beta, const double *z,
+             const double *theta, fsqr_info *out) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!y || !omega || !beta || !z || !theta || !out) return fail(ctx, FSQR_EINVAL, "NULL argument");
+  if (!(tau > 0.0 && tau < 1.0) || !(lambda >= 0.0) || !(lambda_norm > 0.0))
+    return fail(ctx, FSQR_EINVAL, "bad tau/lambda/lambda_norm");
+  Prep pr;
+  TRY(prepare(ctx, Xd, &pr, false));
+  const Dsg &X = pr.X;
+  const int64_t n = X.n, npad = pad16(n), P = X.P;
+  cudaStream_t st = ctx->stream;
+  Fits F = pass_fits(ctx, X);
+  F.nb = 1;
+  double *xb, *th, *ths, *s, *o4, *tc, *tcs, *schk, *summ, *dt, *dl, *om;
+  TRY(wsget(ctx, "k_xbpart", (size_t)kBMaxSplits * npad, &F.xb_part));
+  TRY(wsget(ctx, "k_arb", (size_t)F.gridA, &F.a_rb));
+  TRY(wsget(ctx, "k_act", (size_t)F.gridA, &F.a_ct));
+  TRY(wsget(ctx, "k_acnt", (size_t)F.gridA, &F.a_cnt));
+  TRY(wsget(ctx, "k_alist", (size_t)F.gridA * F.T, &F.a_list));
+  TRY(wsget(ctx, "k_metai", 4, &F.meta_i));
+  TRY(wsget(ctx, "k_metad", kMaxNB, &F.meta_d));
+  int *done;
+  TRY(wsget(ctx, "k_done", kMaxNB, &done));
+  F.done = done;
+  CK(cudaMemsetAsync(done, 0xff, sizeof(int) * kMaxNB, st));
+  TRY(wsget(ctx, "k_xb", (size_t)npad, &xb));
+  TRY(wsget(ctx, "k_th", (size_t)npad, &th));
+  TRY(wsget(ctx, "k_ths", 1, &ths));
+  TRY(wsget(ctx, "k_s", (size_t)P, &s));
+  TRY(wsget(ctx, "k_o4", 4, &o4));
+  TRY(wsget(ctx, "k_tc", (size_t)npad, &tc));
+  TRY(wsget(ctx, "k_tcs", 1, &tcs));
+  TRY(wsget(ctx, "k_schk", (size_t)P, &schk));
+  TRY(wsget(ctx, "k_summ", 8, &summ));
+  TRY(wsget(ctx, "k_tau", 1, &dt));
+  TRY(wsget(ctx, "k_lam", 1, &dl));
+  TRY(wsget(ctx, "k_om", 2, &om));
+  // X~ beta
+  CK(launch_col_pass(A_LIST, 1, X, F, 0, nullptr, nullptr, nullptr, beta, st));
+  CK(launch_xbeta(1, X, F, 0, beta, st));
+  CK(launch_gather_xb(1, F, xb, npad, 1, st));
+  // s = X~^T theta (padded copy of theta)
+  CK(launch_pack(theta, n, th, n, 1, 1, npad, st));
+  CK(launch_sum_cols(th, n, npad, 1, ths, nullptr, st));
+  CK(launch_col_pass(A_XT, 1, X, F, 0, th, ths, s, nullptr, st));
+  CK(launch_kkt_given(n, P, y, xb, z, theta, s, beta, omega, tau, lambda, o4, st));
+  CK(cudaMemcpyAsync(dt, &tau, sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dl, &lambda, sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(launch_min_omega(omega, P, om, st));
+  double hom = 0.0, h4[4];
+  CK(cudaMemcpyAsync(&hom, om, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h4, o4, sizeof h4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  // the summary kernel's loss uses z - r = y - X~ beta; passing y for z and
+  // X~ beta for r gives the primal loss of beta
+  double *ypad;
+  TRY(wsget(ctx, "k_ypad", (size_t)npad, &ypad));
+  CK(launch_pack(y, n, ypad, n, 1, 1, npad, st));
+  const bool gap_def = (P == 1) || (hom > 0.0);
+  const double *schk_use = nullptr, *tc_use = nullptr;
+  if (gap_def) {
+    CK(launch_dual_point(1, th, n, npad, dt, 1, tc, tcs, st));
+    CK(launch_col_pass(A_XT, 1, X, F, 0, tc, tcs, schk, nullptr, st));
+    schk_use = schk;
+    tc_use = tc;
+  }
+  CK(launch_summary(1, 1, n, P, y, ypad, xb, beta, omega, dt, dl, schk_use, tc_use, summ, st));
+  double hs[8];
+  CK(cudaMemcpyAsync(hs, summ, sizeof hs, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  memset(out, 0, sizeof *out);
+  out->r_p = h4[0];
+  out->r_z = h4[1];
+  out->r_beta = h4[2] / lambda_norm;
+  out->r_1 = h4[3];
+  out->kkt = std::max(std::max(out->r_p, out->r_z), std::max(out->r_beta, out->r_1));
+  out->primal = hs[0] + hs[1];
+  out->active = (int64_t)hs[2];
+  if (gap_def) {
+    out->dual = hs[3] * hs[4];
+    out->gap = (out->primal - out->dual) / (1.0 + fabs(out->primal) + fabs(out->dual));
+  } else {
+    out->dual = NAN;
+    out->gap = NAN;
+  }
+  out->lambda = lambda;
+  out->lambda_max = lambda_norm;
+  out->status = FSQR_OK;
+  return FSQR_OK;
+}
+
+int fsqr_predict(fsqr_ctx *ctx, const fsqr_design *Xd, const double *beta, int B, double *out) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!beta || !out || B < 0) return fail(ctx, FSQR_EINVAL, "bad arguments");
+  if (B == 0) return FSQR_OK;
+  Prep pr;
+  TRY(prepare(ctx, Xd, &pr, false));
+  const Dsg &X = pr.X;
+  const int64_t n = X.n, npad = pad16(n), P = X.P;
+  cudaStream_t st = ctx->stream;
+  Fits F = pass_fits(ctx, X);
+  TRY(wsget(ctx, "p_xbpart", (size_t)kBMaxSplits * npad * kMaxNB, &F.xb_part));
+  TRY(wsget(ctx, "p_arb", (size_t)F.gridA * kMaxNB, &F.a_rb));
+  TRY(wsget(ctx, "p_act", (size_t)F.gridA * kMaxNB, &F.a_ct));
+  TRY(wsget(ctx, "p_acnt", (size_t)F.gridA, &F.a_cnt));
+  TRY(wsget(ctx, "p_alist", (size_t)F.gridA * F.T, &F.a_list));
+  TRY(wsget(ctx, "p_metai", 4, &F.meta_i));
+  TRY(wsget(ctx, "p_metad", kMaxNB, &F.meta_d));
+  int *done;
+  TRY(wsget(ctx, "p_done", kMaxNB, &done));
+  F.done = done;
+  CK(cudaMemsetAsync(done, 0xff, sizeof(int) * kMaxNB, st));
+  double *bg;
+  TRY(wsget(ctx, "p_bg", (size_t)P * kMaxNB, &bg));
+  CK(cudaMemsetAsync(bg, 0, sizeof(double) * P * kMaxNB, st));
+  for (int b0 = 0; b0 < B; b0 += kMaxNB) {
+    const int nb = std::min(kMaxNB, B - b0);
+    const int NB = nb_template(nb);
+    F.nb = nb;
+    CK(launch_pack(beta + (int64_t)b0 * P, P, bg, P, nb, NB, P, st));
+    CK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, bg, st));
+    CK(launch_xbeta(NB, X, F, 0, bg, st));
+    CK(launch_gather_xb(NB, F, out + (int64_t)b0 * n, n, nb, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return FSQR_OK;
+}
+
+int fsqr_profile_enable(fsqr_ctx *ctx, int on) {
+  if (!ctx) return FSQR_EINVAL;
+  ctx->prof = on != 0;
+  return FSQR_OK;
+}
+
+int fsqr_profile_get(fsqr_ctx *ctx, fsqr_profile *out) {
+  if (!ctx || !out) return FSQR_EINVAL;
+  *out = ctx->pf;
+  return FSQR_OK;
+}
+
+int fsqr_profile_reset(fsqr_ctx *ctx) {
+  if (!ctx) return FSQR_EINVAL;
+  ctx->pf = fsqr_profile{};
+  return FSQR_OK;
+}
+
+int fsqr_back_transform(fsqr_ctx *ctx, const fsqr_design *Xd, const double *beta_std, int B,
+                        double *beta_out) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!beta_std || !beta_out || B < 0) return fail(ctx, FSQR_EINVAL, "bad arguments");
+  Prep pr;
+  TRY(prepare(ctx, Xd, &pr, false));
+  CK(launch_back_transform(pr.X, beta_std, B, beta_out, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSQR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Internal declarations shared by the FS-QRPPA kernels and the C-ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fsqr.h"
+
+namespace fsqr {
+
+constexpr int kMaxNB = 8;          // fits advanced together per X pass
+constexpr int kAThreads = 256;     // column kernel: 8 warps
+constexpr int kAWarps = kAThreads / 32;
+constexpr int kACols = 4;          // columns register-blocked per warp
+constexpr int kBThreads = 256;     // X~ beta kernel
+constexpr int kBRowsPerThread = 8;
+constexpr int kBRows = kBThreads * kBRowsPerThread;
+constexpr int kBMaxSplits = 64;
+constexpr int kBMinColsPerSplit = 16;
+constexpr int kCThreads = 128;     // vector-update kernel
+constexpr int kCPartials = 4;      // r_p max, r_z max, sum theta, max |theta|
+constexpr int kReport = 8;         // kkt, r_p, r_z, r_b, r_1, status, bound, iters
+
+// Column kernel modes.
+enum AMode { A_PROX = 0, A_XT = 1, A_XT_BLOCK = 2, A_LIST = 3 };
+
+// The standardised design as the kernels see it. Column j in [0, P):
+// x~_ij = a[j] * x_ij + b[j] for an observed entry; a[0] = 0, b[0] = 1
+// makes column 0 the intercept. 1 <= j <= c: x_ij = cov[(j-1)*n + i];
+// j > c: stored column j-1-c.
+struct Dsg {
+  int64_t n, p, c, P;
+  int fmt;
+  const uint8_t *geno;
+  int64_t ld;
+  const double *cov;
+  const double *a;
+  const double *b;
+};
+
+// State and parameters of a group of NB fits advanced together.
+// Per-column arrays are interleaved by fit: v[j*NB + b]; per-sample arrays
+// likewise v[i*NB + b] with npad >= n rows whose padding stays 0.
+struct Fits {
+  int nb;                 // live fits in the group (<= NB); slots >= nb are idle
+  int64_t n;              // samples
+  int64_t npad;           // rows of the per-sample arrays (multiple of 16)
+  const double *y;        // n
+  double ymax;            // ||y||_inf
+  const double *omega;    // P
+  double *beta[2];        // P*NB each; iterate k lives in beta[k & 1]
+  double *z, *theta, *r;  // npad*NB
+  const int64_t *block_ptr;
+  int G;
+  const double *eta;      // G
+  const double *inv_eta;  // G
+  double tau[kMaxNB], lam[kMaxNB], lamnorm[kMaxNB];
+  double mu, sigma, tol;
+  int K, max_iter;
+  // column-kernel outputs, one slot per CTA of the column kernel
+  int gridA, T;
+  double *a_rb;   // gridA*NB: max_j dist(s_j, lam_j d|beta_j|)
+  double *a_ct;   // gridA*NB: sum_j b_j beta_j (constant part of X~ beta)
+  int *a_cnt;     // gridA: active columns found by the CTA
+  int *a_list;    // gridA*T: those columns, ascending
+  // X~ beta partial sums and their bookkeeping
+  double *xb_part;  // kBMaxSplits * npad * NB
+  int *meta_i;      // [0] = splits used by the last X~ beta pass
+  double *meta_d;   // [0..NB) = constant term of the last X~ beta pass
+  // vector-kernel partials of the iterate of each parity
+  int gridC;
+  double *c_part[2];  // gridC * NB * kCPartials
+  // per-fit status
+  int *done;        // NB: iteration whose iterate is final, -1 while running
+  int *n_done;      // counter of finished fits
+  double *report;   // NB * kReport
+  const int *it_base;
+  // mixed precision
+  int mixed, D;
+  int64_t n4p;      // digit words per (fit, digit) row = npad / 4
+  int32_t *digits;  // NB * D * n4p words, 4 samples per word
+  double *scale;    // NB: quantisation scale 2^e
+  double colbound;  // max_j a_j * sum_i |x_ij| over stored columns
+};
+
+// ---- launchers (kernels.cu) -------------------------------------------------
+cudaError_t launch_col_stats(const Dsg &X, double *mean, double *sd, int *missing,
+                             cudaStream_t s);
+cudaError_t launch_affine(const Dsg &X, const double *mean, const double *sd, int standardize,
+                          double *a, double *b, cudaStream_t s);
+cudaError_t launch_colbound(const Dsg &X, const double *mean, double *out, cudaStream_t s);
+
+// One pass over all columns; see kernels.cu for the four modes.
+cudaError_t launch_col_pass(int mode, int NB, const Dsg &X, const Fits &F, int off,
+                            const double *vec, const double *vsum, double *s_out,
+                            const double *beta_in, cudaStream_t s);
+size_t col_pass_smem(int mode, const Fits &F, int NB);
+int col_pass_occupancy(int NB, int mixed, int D, size_t smem);
+cudaError_t launch_xbeta(int NB, const Dsg &X, const Fits &F, int off, const double *beta_in,
+                         cudaStream_t s);
+cudaError_t launch_quantize(int NB, const Fits &F, int off, cudaStream_t s);
+cudaError_t launch_check(int NB, const Fits &F, int off, cudaStream_t s);
+cudaError_t launch_vec(int NB, const Fits &F, int off, int init, cudaStream_t s);
+cudaError_t launch_advance(int *it_base, int M, cudaStream_t s);
+cudaError_t launch_gather_xb(int NB, const Fits &F, double *out, int64_t ldo, int nb,
+                             cudaStream_t s);  // out[b*ldo + i], i < F.n
+
+// Setup and reporting helpers (k_setup.cu).
+cudaError_t launch_vec_stats(const double *v, int64_t n, double *out3, cudaStream_t s);
+cudaError_t launch_sum_cols(const double *v, int64_t n, int64_t ldv, int nvec, double *sums,
+                            double *sqsums, cudaStream_t s);
+cudaError_t launch_select(const double *y, int64_t n, int64_t k, double *out, cudaStream_t s);
+cudaError_t launch_lmax_vec(const double *y, int64_t n, int64_t npad, double tau,
+                            const double *q, double *v, cudaStream_t s);
+cudaError_t launch_colmax_ratio(const double *s_col, const double *omega, int64_t P,
+                                double scale, double *out, cudaStream_t s);
+cudaError_t launch_power_init(double *v, const int64_t *block_ptr, int G, int64_t P,
+                              cudaStream_t s);
+cudaError_t launch_power_step(const double *w, const int64_t *block_ptr, int G, int64_t P,
+                              double *v, double *wnorm, cudaStream_t s);
+cudaError_t launch_xv_blocks(const Dsg &X, const double *v, const int64_t *splits,
+                             const int *split_of_block, int G, int nsplit, double *u,
+                             int64_t npad, double *part, cudaStream_t s);
+cudaError_t launch_pack(const double *src, int64_t lds, double *dst, int64_t len, int nb,
+                        int NB, int64_t dst_rows, cudaStream_t s);
+cudaError_t launch_unpack(const double *src, double *dst, int64_t lds, int64_t len, int nb,
+                          int NB, cudaStream_t s);
+cudaError_t launch_fill(double *p, double v, int64_t n, cudaStream_t s);
+cudaError_t launch_init_state(int NB, const Fits &F, int nb, int warm, cudaStream_t s);
+cudaError_t launch_dual_point(int NB, const double *theta, int64_t n, int64_t npad,
+                              const double *taus, int nb, double *out, double *sums,
+                              cudaStream_t s);
+cudaError_t launch_min_omega(const double *omega, int64_t P, double *out, cudaStream_t s);
+cudaError_t launch_summary(int NB, int nb, int64_t n, int64_t P, const double *y,
+                           const double *z, const double *r, const double *beta,
+                           const double *omega, const double *taus, const double *lams,
+                           const double *s_chk, const double *tc, double *out, cudaStream_t s);
+cudaError_t launch_kkt_given(int64_t n, int64_t P, const double *y, const double *xb,
+                             const double *z, const double *theta, const double *s,
+                             const double *beta, const double *omega, double tau, double lam,
+                             double *out, cudaStream_t st);
+cudaError_t launch_back_transform(const Dsg &X, const double *beta, int B, double *out,
+                                  cudaStream_t s);
+
+}  // namespace fsqr

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of the C ABI in include/fsqr.h (libfsqr.so).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels. Device arrays are torch CUDA tensors (float64 / uint8 / int8,
+contiguous); host arrays are numpy. The in-tree library must have been built
+(paper_2601_02826_gb300.build.build()); nothing here falls back to any other
+implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOCONV, ETIMEOUT, ENUMERIC, ECUDA, ENOMEM = range(7)
+DENSE_F64, INT8, TWOBIT = 0, 1, 2
+FP64, MIXED = 0, 1
+WARM_NONE, WARM_GIVEN, WARM_PATH = 0, 1, 2
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOCONV", 3: "ETIMEOUT", 4: "ENUMERIC", 5: "ECUDA", 6: "ENOMEM"}
+
+
+class Design(C.Structure):
+    _fields_ = [("n", C.c_int64), ("p", C.c_int64), ("c", C.c_int64),
+                ("geno_format", C.c_int32), ("standardize", C.c_int32),
+                ("geno", C.c_void_p), ("geno_ld", C.c_int64), ("cov", C.c_void_p),
+                ("col_mean", C.c_void_p), ("col_sd", C.c_void_p)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
+                ("mu", C.c_double), ("eta", C.POINTER(C.c_double)), ("eta_margin", C.c_double),
+                ("power_iters", C.c_int32), ("power_tol", C.c_double), ("precision", C.c_int32),
+                ("warm", C.c_int32), ("digits", C.c_int32), ("max_group", C.c_int32),
+                ("timeout_ms", C.c_int64)]
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("kkt", C.c_double),
+                ("r_p", C.c_double), ("r_z", C.c_double), ("r_beta", C.c_double),
+                ("r_1", C.c_double), ("primal", C.c_double), ("dual", C.c_double),
+                ("gap", C.c_double), ("lambda_", C.c_double), ("lambda_max", C.c_double),
+                ("mu", C.c_double), ("active", C.c_int64), ("t_setup_ms", C.c_double),
+                ("t_solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(C.Structure):
+    _fields_ = [("col_samples", C.c_int64), ("col_ms", C.c_double), ("xb_samples", C.c_int64),
+                ("xb_ms", C.c_double), ("vec_samples", C.c_int64), ("vec_ms", C.c_double),
+                ("iterations", C.c_int64), ("kernel_launches", C.c_int64), ("col_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["fsqr_version", "fsqr_opts_default", "fsqr_create", "fsqr_destroy", "fsqr_last_error",
+           "fsqr_col_stats", "fsqr_lambda_max", "fsqr_eta", "fsqr_fit", "fsqr_fit_batch",
+           "fsqr_fit_batch_host", "fsqr_kkt", "fsqr_predict", "fsqr_back_transform",
+           "fsqr_profile_enable", "fsqr_profile_get", "fsqr_profile_reset"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Loads libfsqr.so (building it first if needed); raises if impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        _build.build()
+    L = C.CDLL(p)
+    vp, i32, i64, dbl, pd = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.POINTER(C.c_double)
+    pD, pO, pI = C.POINTER(Design), C.POINTER(Opts), C.POINTER(Info)
+    pi64 = C.POINTER(C.c_int64)
+    L.fsqr_version.restype = i32
+    L.fsqr_opts_default.argtypes = [pO]
+    L.fsqr_opts_default.restype = None
+    L.fsqr_create.argtypes = [C.POINTER(vp), i32, vp]
+    L.fsqr_destroy.argtypes = [vp]
+    L.fsqr_last_error.argtypes = [vp]
+    L.fsqr_last_error.restype = C.c_char_p
+    L.fsqr_col_stats.argtypes = [vp, pD, vp, vp]
+    L.fsqr_lambda_max.argtypes = [vp, pD, vp, dbl, vp, pd]
+    L.fsqr_eta.argtypes = [vp, pD, pi64, i32, dbl, dbl, i32, dbl, pd]
+    L.fsqr_fit.argtypes = [vp, pD, vp, dbl, dbl, vp, pi64, i32, pO, vp, vp, vp, pI]
+    L.fsqr_fit_batch.argtypes = [vp, pD, vp, i32, pd, i32, pd, vp, pi64, i32, pO, vp, vp, vp, pI]
+    L.fsqr_fit_batch_host.argtypes = [vp, pD, vp, i32, pd, i32, pd, vp, pi64, i32, pO, vp, vp, vp, pI]
+    L.fsqr_kkt.argtypes = [vp, pD, vp, dbl, dbl, vp, dbl, vp, vp, vp, pI]
+    L.fsqr_predict.argtypes = [vp, pD, vp, i32, vp]
+    L.fsqr_back_transform.argtypes = [vp, pD, vp, i32, vp]
+    L.fsqr_profile_enable.argtypes = [vp, i32]
+    L.fsqr_profile_get.argtypes = [vp, C.POINTER(Profile)]
+    L.fsqr_profile_reset.argtypes = [vp]
+    for f in EXPORTS:
+        if f not in ("fsqr_opts_default", "fsqr_last_error", "fsqr_version"):
+            getattr(L, f).restype = i32
+    _lib = L
+    return L
+
+
+class FsqrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a):
+    """Host address of a numpy array or a CPU (ideally pinned) torch tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def default_opts(**kw) -> Opts:
+    L = load()
+    o = Opts()
+    L.fsqr_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "eta":
+            continue
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """A library context bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.L = load()
+        h = C.c_void_p()
+        s = C.c_void_p(stream) if stream else None
+        rc = self.L.fsqr_create(C.byref(h), device, s)
+        if rc != OK:
+            raise FsqrError(rc, "fsqr_create failed")
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.fsqr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allowed=(OK,)):
+        if rc not in allowed:
+            raise FsqrError(rc, self.L.fsqr_last_error(self.h).decode())
+        return rc
+
+    # ------------------------------------------------------------- designs
+    def design(self, n, p, c, fmt, geno, ld, cov=None, col_mean=None, col_sd=None, standardize=1,
+               host=False):
+        d = Design()
+        d.n, d.p, d.c = n, p, c
+        d.geno_format, d.standardize = fmt, standardize
+        ptr = _host_ptr if host else _ptr
+        d.geno = ptr(geno) if geno is not None else None
+        d.geno_ld = ld
+        d.cov = ptr(cov) if (cov is not None and c > 0) else None
+        d.col_mean = ptr(col_mean) if col_mean is not None else None
+        d.col_sd = ptr(col_sd) if col_sd is not None else None
+        self._keep.append((geno, cov, col_mean, col_sd))
+        return d
+
+    # ---------------------------------------------------------- functions
+    def col_stats(self, d, mean_out, sd_out):
+        self._check(self.L.fsqr_col_stats(self.h, C.byref(d), _ptr(mean_out), _ptr(sd_out)))
+
+    def lambda_max(self, d, y, tau, omega) -> float:
+        out = C.c_double()
+        self._check(self.L.fsqr_lambda_max(self.h, C.byref(d), _ptr(y), tau, _ptr(omega), C.byref(out)))
+        return out.value
+
+    def eta(self, d, block_ptr, mu, margin=0.05, max_iter=100, tol=1e-6) -> np.ndarray:
+        bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
+        G = len(bp) - 1
+        out = np.zeros(max(G, 1))
+        self._check(self.L.fsqr_eta(self.h, C.byref(d), bp.ctypes.data_as(C.POINTER(C.c_int64)), G,
+                                    mu, margin, max_iter, tol, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out[:G]
+
+    def _opts(self, opts: dict | None, G: int):
+        o = default_opts(**(opts or {}))
+        eta = None
+        if opts and opts.get("eta") is not None:
+            eta = np.ascontiguousarray(opts["eta"], dtype=np.float64)
+            assert len(eta) == G
+            o.eta = eta.ctypes.data_as(C.POINTER(C.c_double))
+        return o, eta
+
+    def fit(self, d, y, tau, lam, omega, block_ptr, beta, z, theta, opts=None,
+            allowed=(OK, ENOCONV, ETIMEOUT)):
+        bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
+        G = len(bp) - 1
+        o, keep = self._opts(opts, G)
+        info = Info()
+        rc = self.L.fsqr_fit(self.h, C.byref(d), _ptr(y), tau, lam, _ptr(omega),
+                             bp.ctypes.data_as(C.POINTER(C.c_int64)), G, C.byref(o),
+                             _ptr(beta), _ptr(z), _ptr(theta), C.byref(info))
+        self._check(rc, allowed)
+        return rc, info
+
+    def fit_batch(self, d, y, taus, lambdas, omega, block_ptr, beta, z, theta, opts=None,
+                  allowed=(OK, ENOCONV, ETIMEOUT), host=False):
+        taus = np.ascontiguousarray(taus, dtype=np.float64)
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        n_tau = len(taus)
+        n_lambda = lam.size // n_tau
+        assert lam.size == n_tau * n_lambda
+        bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
+        G = len(bp) - 1
+        o, keep = self._opts(opts, G)
+        infos = (Info * (n_tau * n_lambda))()
+        fn = self.L.fsqr_fit_batch_host if host else self.L.fsqr_fit_batch
+        ptr = _host_ptr if host else _ptr
+        rc = fn(self.h, C.byref(d), ptr(y), n_tau, taus.ctypes.data_as(C.POINTER(C.c_double)),
+                n_lambda, lam.ctypes.data_as(C.POINTER(C.c_double)), ptr(omega),
+                bp.ctypes.data_as(C.POINTER(C.c_int64)), G, C.byref(o), ptr(beta), ptr(z), ptr(theta),
+                infos)
+        self._check(rc, allowed)
+        return rc, list(infos)
+
+    def kkt(self, d, y, tau, lam, omega, lam_norm, beta, z, theta) -> Info:
+        info = Info()
+        self._check(self.L.fsqr_kkt(self.h, C.byref(d), _ptr(y), tau, lam, _ptr(omega), lam_norm,
+                                    _ptr(beta), _ptr(z), _ptr(theta), C.byref(info)))
+        return info
+
+    def predict(self, d, beta, B, out):
+        self._check(self.L.fsqr_predict(self.h, C.byref(d), _ptr(beta), B, _ptr(out)))
+
+    def back_transform(self, d, beta_std, B, out):
+        self._check(self.L.fsqr_back_transform(self.h, C.byref(d), _ptr(beta_std), B, _ptr(out)))
+
+    def profile(self, enable: bool | None = None, reset: bool = False) -> Profile:
+        if enable is not None:
+            self.L.fsqr_profile_enable(self.h, 1 if enable else 0)
+        if reset:
+            self.L.fsqr_profile_reset(self.h)
+        p = Profile()
+        self.L.fsqr_profile_get(self.h, C.byref(p))
+        return p
+
+    def last_error(self) -> str:
+        return self.L.fsqr_last_error(self.h).decode()
