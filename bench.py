@@ -158,6 +158,9 @@ def run_gb300(args, rank, world, local_rank):
     z = torch.zeros(B * w.n, dtype=torch.float64, device=dev)
     th = torch.zeros(B * w.n, dtype=torch.float64, device=dev)
     mixed = dict(tol=TOL, precision=fsqr.MIXED, digits=4, max_group=B)
+    if args.profile_iters:
+        # bounded run for profilers: fixed iteration count, no stop at tol
+        mixed.update(tol=0.0, max_iter=args.profile_iters)
 
     def step(opts, infos_out=None):
         lam = [LAMBDA_FRAC * ctx.lambda_max(dw.design, dw.y, t, dw.omega) for t in TAUS]
@@ -181,7 +184,7 @@ def run_gb300(args, rank, world, local_rank):
         t_wall = time.perf_counter()
         for _ in range(args.steps):
             rc = step(mixed, infos)
-            assert rc == fsqr.OK, (rc, [i.as_dict() for i in infos[-B:]])
+            assert rc == fsqr.OK or args.profile_iters, (rc, [i.as_dict() for i in infos[-B:]])
         e1.record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -206,23 +209,33 @@ def run_gb300(args, rank, world, local_rank):
     iters = [i.iters for i in infos[-B:]]
     kkts = [i.kkt for i in infos[-B:]]
 
-    # plain FP64 GPU FS-QRPPA: one fit at a time, cold start (comparison)
+    # plain FP64 GPU FS-QRPPA: one fit at a time, cold start (comparison).
+    # Timed on a bounded number of iterations per fit and scaled by the
+    # iterations the fits need (the same algorithm; FP64 products).
     fp64 = None
-    if not args.skip_fp64 and rank == 0:
-        fp_opts = dict(tol=TOL, precision=fsqr.FP64, max_group=1)
+    if not args.skip_fp64 and rank == 0 and not args.profile_iters:
+        n_it = args.fp64_iters
+        fp_opts = dict(tol=0.0, max_iter=n_it, precision=fsqr.FP64, max_group=1)
+        ctx.profile(enable=True, reset=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         inf64 = []
-        rc = step(fp_opts, inf64)
+        step(fp_opts, inf64)
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
-        fp64 = {"value": B / t64, "unit": UNIT, "ms_per_step": t64 * 1e3,
-                "iters": [i.iters for i in inf64], "kkt": [i.kkt for i in inf64],
+        p64 = ctx.profile(enable=False)
+        s_per_iter = t64 / (B * n_it)
+        need = float(np.mean(iters))
+        fp64 = {"value": 1.0 / (s_per_iter * need), "unit": UNIT,
+                "ms_per_iteration": s_per_iter * 1e3, "iterations_scaled_to": need,
+                "col_launch_ms": p64.col_ms / max(1, p64.col_samples),
+                "sample": f"{B} fits x {n_it} iterations timed (setup included), scaled to the "
+                          f"mean iteration count of the timed mixed fits",
                 "precision": "fp64", "max_group": 1}
 
     # end to end through the host-buffer entry point (copies inside the call)
     e2e = None
-    if not args.skip_e2e:
+    if not args.skip_e2e and not args.profile_iters:
         gh = torch.from_numpy(np.ascontiguousarray(w.geno).view(np.uint8)).pin_memory()
         ch = torch.from_numpy(np.ascontiguousarray(w.cov)).pin_memory()
         yh = torch.from_numpy(w.y.copy()).pin_memory()
@@ -249,7 +262,7 @@ def run_gb300(args, rank, world, local_rank):
                "note": "fsqr_fit_batch_host from pinned host buffers; lambda from a device call"}
 
     cpu = None
-    if rank == 0 and not args.skip_cpu:
+    if rank == 0 and not args.skip_cpu and not args.profile_iters:
         cpu = cpu_baseline(w, iters)
 
     out = {
@@ -278,6 +291,9 @@ def run_gb300(args, rank, world, local_rank):
     }
     if fp64:
         out["vs_fp64_plain"] = value / fp64["value"]
+    if args.profile_iters:
+        out["profile_run"] = f"fixed {args.profile_iters} iterations per fit; not a benchmark result"
+
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
@@ -350,6 +366,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=3000)
+    ap.add_argument("--fp64-iters", type=int, default=400)
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiling run: every fit stops after this many iterations (not a bench line)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

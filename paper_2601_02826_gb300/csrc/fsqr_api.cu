@@ -430,6 +430,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   F.max_iter = E.o->max_iter;
   F.mixed = mixed ? 1 : 0;
   F.D = mixed ? E.o->digits : 0;
+  F.DW = mixed ? 6 : 0;
   F.n4p = npad / 4;
   F.colbound = E.pr->colbound;
   // tiling from the occupancy of the kernel this group runs
@@ -467,6 +468,8 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   if (mixed) {
     TRY(wsget(ctx, "g_digits", (size_t)NB * F.D * F.n4p, &F.digits));
     TRY(wsget(ctx, "g_scale", kMaxNB, &F.scale));
+    TRY(wsget(ctx, "g_xbipart", (size_t)kBMaxSplits * npad * NB, &F.xb_ipart));
+    TRY(wsget(ctx, "g_awmax", (size_t)F.gridA * NB, &F.a_wmax));
   }
   const size_t smem = col_pass_smem(A_PROX, F, NB);
   if (smem > 227 * 1024)
@@ -497,34 +500,40 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   }
   CK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, F.beta[0], st));
   CK(launch_xbeta(NB, X, F, 0, F.beta[0], st));
-  CK(launch_vec(NB, F, 0, 1, st));
+  CK(launch_vec(NB, X, F, 0, 1, st));
 
   // ---- the iteration as a captured graph of M steps
   const int K = F.K;
   const int M = K * std::max(1, (20 + K - 1) / K);
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
   const bool prof = ctx->prof;
   if (prof && !ctx->ev[0])
     for (int e = 0; e < 6; ++e) CK(cudaEventCreate(&ctx->ev[e]));
-  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  cudaError_t ce = cudaSuccess;
   int per_graph = 1;  // the advance kernel
-  for (int off = 0; off < M && ce == cudaSuccess; ++off) {
-    const bool sample = prof && off == 1;
-    if (mixed && ce == cudaSuccess) ce = launch_quantize(NB, F, off, st);
-    if (sample && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[0], st);
-    if (ce == cudaSuccess) ce = launch_col_pass(A_PROX, NB, X, F, off, nullptr, nullptr, nullptr, nullptr, st);
-    if (sample && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[1], st);
-    if (ce == cudaSuccess) ce = launch_xbeta(NB, X, F, off, nullptr, st);
-    if (sample && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], st);
-    if (off % K == 0 && ce == cudaSuccess) ce = launch_check(NB, F, off, st);
-    if (sample && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[3], st);
-    if (ce == cudaSuccess) ce = launch_vec(NB, F, off, 0, st);
-    if (sample && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[4], st);
-    per_graph += 3 + (mixed ? 1 : 0) + (off % K == 0 ? 1 : 0);
-  }
-  if (ce == cudaSuccess) ce = launch_advance(it_base, M, st);
+  for (int off = 0; off < M; ++off) per_graph += 3 + (mixed ? 1 : 0) + (off % K == 0 ? 1 : 0);
+  // Enqueues steps base..base+M-1 (kernels read the base from it_base); with
+  // sample set, events bracket the kernels of the second step.
+  auto enqueue = [&](bool sample) -> cudaError_t {
+    cudaError_t ce = cudaSuccess;
+    for (int off = 0; off < M && ce == cudaSuccess; ++off) {
+      const bool sm = sample && off == 1;
+      if (mixed) ce = launch_quantize(NB, F, off, st);
+      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[0], st);
+      if (ce == cudaSuccess) ce = launch_col_pass(A_PROX, NB, X, F, off, nullptr, nullptr, nullptr, nullptr, st);
+      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[1], st);
+      if (ce == cudaSuccess) ce = launch_xbeta(NB, X, F, off, nullptr, st);
+      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], st);
+      if (off % K == 0 && ce == cudaSuccess) ce = launch_check(NB, F, off, st);
+      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[3], st);
+      if (ce == cudaSuccess) ce = launch_vec(NB, X, F, off, 0, st);
+      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[4], st);
+    }
+    if (ce == cudaSuccess) ce = launch_advance(it_base, M, st);
+    return ce;
+  };
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = enqueue(false);
   cudaError_t ee = cudaStreamEndCapture(st, &graph);
   if (ce != cudaSuccess || ee != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -544,7 +553,9 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   int host_base = 0;
   int rc = FSQR_OK;
   for (int64_t l = 0;; ++l) {
-    ce = cudaGraphLaunch(exec, st);
+    // every 8th replay runs eagerly with events around one step's kernels
+    const bool sample = prof && (l % 8 == 0);
+    ce = sample ? enqueue(true) : cudaGraphLaunch(exec, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(hdone, F.n_done, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) {
@@ -553,7 +564,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     }
     host_base += M;
     ctx->pf.kernel_launches += per_graph;
-    if (prof) {
+    if (sample) {
       float a = 0.f, b = 0.f, c = 0.f;
       if (cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]) == cudaSuccess &&
           cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]) == cudaSuccess &&

@@ -64,9 +64,11 @@ struct Fits {
   int *a_cnt;     // gridA: active columns found by the CTA
   int *a_list;    // gridA*T: those columns, ascending
   // X~ beta partial sums and their bookkeeping
-  double *xb_part;  // kBMaxSplits * npad * NB
-  int *meta_i;      // [0] = splits used by the last X~ beta pass
-  double *meta_d;   // [0..NB) = constant term of the last X~ beta pass
+  double *xb_part;  // kBMaxSplits * npad * NB (FP64 path)
+  long long *xb_ipart;  // kBMaxSplits * npad * NB exact integer partials (mixed path)
+  double *a_wmax;   // gridA*NB: max |a_j beta_j| over stored columns (mixed path)
+  int *meta_i;      // [0] = splits used by the last X~ beta pass, [1] = active columns
+  double *meta_d;   // [0..NB) constant term, [kMaxNB..kMaxNB+NB) integer scale of the last pass
   // vector-kernel partials of the iterate of each parity
   int gridC;
   double *c_part[2];  // gridC * NB * kCPartials
@@ -77,6 +79,7 @@ struct Fits {
   const int *it_base;
   // mixed precision
   int mixed, D;
+  int DW;           // digits of the X~ beta weights in the mixed path
   int64_t n4p;      // digit words per (fit, digit) row = npad / 4
   int32_t *digits;  // NB * D * n4p words, 4 samples per word
   double *scale;    // NB: quantisation scale 2^e
@@ -100,10 +103,10 @@ cudaError_t launch_xbeta(int NB, const Dsg &X, const Fits &F, int off, const dou
                          cudaStream_t s);
 cudaError_t launch_quantize(int NB, const Fits &F, int off, cudaStream_t s);
 cudaError_t launch_check(int NB, const Fits &F, int off, cudaStream_t s);
-cudaError_t launch_vec(int NB, const Fits &F, int off, int init, cudaStream_t s);
+cudaError_t launch_vec(int NB, const Dsg &X, const Fits &F, int off, int init, cudaStream_t s);
 cudaError_t launch_advance(int *it_base, int M, cudaStream_t s);
 cudaError_t launch_gather_xb(int NB, const Fits &F, double *out, int64_t ldo, int nb,
-                             cudaStream_t s);  // out[b*ldo + i], i < F.n
+                             cudaStream_t s);  // out[b*ldo + i], i < F.n (FP64 path)
 
 // Setup and reporting helpers (k_setup.cu).
 cudaError_t launch_vec_stats(const double *v, int64_t n, double *out3, cudaStream_t s);

@@ -14,6 +14,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "fsqr_internal.h"
 
 namespace fsqr {
@@ -193,9 +195,9 @@ __device__ __forceinline__ void dot4_int8_digits(const Dsg &X, const uint8_t *co
       for (int d = 0; d < D; ++d) acc[q][b][d] = 0;
   const int64_t nch = (X.n + 15) >> 4;
   for (int64_t ch = lane; ch < nch; ch += 32) {
-    uint4 gv[kACols];
+    uint4 cur[kACols];
 #pragma unroll
-    for (int q = 0; q < kACols; ++q) gv[q] = __ldcs(reinterpret_cast<const uint4 *>(cp[q]) + ch);
+    for (int q = 0; q < kACols; ++q) cur[q] = __ldcs(reinterpret_cast<const uint4 *>(cp[q]) + ch);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
 #pragma unroll
@@ -204,10 +206,10 @@ __device__ __forceinline__ void dot4_int8_digits(const Dsg &X, const uint8_t *co
 #pragma unroll
         for (int q = 0; q < kACols; ++q) {
           int a = acc[q][b][d];
-          a = __dp4a((int)gv[q].x, tw.x, a);
-          a = __dp4a((int)gv[q].y, tw.y, a);
-          a = __dp4a((int)gv[q].z, tw.z, a);
-          a = __dp4a((int)gv[q].w, tw.w, a);
+          a = __dp4a((int)cur[q].x, tw.x, a);
+          a = __dp4a((int)cur[q].y, tw.y, a);
+          a = __dp4a((int)cur[q].z, tw.z, a);
+          a = __dp4a((int)cur[q].w, tw.w, a);
           acc[q][b][d] = a;
         }
       }
@@ -231,7 +233,7 @@ __device__ __forceinline__ void dot4_int8_digits(const Dsg &X, const uint8_t *co
 //   A_XT_BLOCK : NB = 1, column j uses v = vec + block(j)*npad, vsum[block(j)]
 //   A_LIST     : lists and constant terms of beta_in, no data read
 template <int NB, int MODE, int D>
-__global__ void __launch_bounds__(kAThreads)
+__global__ void __launch_bounds__(kAThreads, ((D > 0 && NB * D <= 12) ? 2 : 1))
     k_col(Dsg X, Fits F, int off, const double *__restrict__ vec, const double *__restrict__ vsum,
           double *__restrict__ s_out, const double *__restrict__ beta_in) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -246,6 +248,7 @@ __global__ void __launch_bounds__(kAThreads)
   __shared__ int sIdle[kMaxNB];
   __shared__ double red_rb[kAWarps][32];
   __shared__ double red_ct[kAWarps][32];
+  __shared__ double red_wm[kAWarps][32];
   __shared__ int scan[kAThreads];
 
   int k = 0;
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(kAThreads)
 
   const int mycol = lane / NB, myb = lane % NB;
   const bool lane_has = lane < kACols * NB;
-  double rbl = 0.0, ctl = 0.0;
+  double rbl = 0.0, ctl = 0.0, wml = 0.0;
 
   for (int64_t jg = j0 + warp * kACols; jg < j1; jg += kAWarps * kACols) {
     double tot[kACols][NB];
@@ -353,6 +356,7 @@ __global__ void __launch_bounds__(kAThreads)
         if (!sIdle[myb]) {
           ctl = fma(bj, bv, ctl);
           act = (bv != 0.0) && jq >= 1;
+          if (jq > X.c) wml = fmax(wml, fabs(aj * bv));
         }
       } else {  // A_PROX
         const double s = aj * mydot + bj * sS[myb];
@@ -368,6 +372,7 @@ __global__ void __launch_bounds__(kAThreads)
           bnxt[jq * NB + myb] = bn;
           ctl = fma(bj, bn, ctl);
           act = (bn != 0.0) && jq >= 1;
+          if (jq > X.c) wml = fmax(wml, fabs(aj * bn));
         }
       }
     }
@@ -385,17 +390,20 @@ __global__ void __launch_bounds__(kAThreads)
   // Per-CTA reductions in a fixed order (deterministic).
   red_rb[warp][lane] = rbl;
   red_ct[warp][lane] = ctl;
+  red_wm[warp][lane] = wml;
   __syncthreads();
   if (threadIdx.x < NB) {
     const int b = threadIdx.x;
-    double m = 0.0, c = 0.0;
+    double m = 0.0, c = 0.0, wm = 0.0;
     for (int w = 0; w < kAWarps; ++w)
       for (int q = 0; q < kACols; ++q) {
         m = fmax(m, red_rb[w][q * NB + b]);
         c += red_ct[w][q * NB + b];
+        wm = fmax(wm, red_wm[w][q * NB + b]);
       }
     F.a_rb[blockIdx.x * NB + b] = m;
     F.a_ct[blockIdx.x * NB + b] = c;
+    if (F.a_wmax) F.a_wmax[blockIdx.x * NB + b] = wm;
   }
   // Ordered compaction of the active flags.
   const int per = (T + kAThreads - 1) / kAThreads;
@@ -575,9 +583,189 @@ __global__ void __launch_bounds__(kBThreads)
       for (int b = 0; b < NB; ++b) out[(i0 + r) * NB + b] = acc[r][b];
 }
 
+// Mixed path: exact integer X~ beta over the active stored columns.
+// w_jb = a_j beta_jb is rounded to a 7*DW-bit fixed-point integer W_jb with
+// the per-fit scale 2^(E_b+1) (max_j |w_jb| < 2^E_b over the stored active
+// columns, from the column pass), split into DW balanced int8 digits. For 4
+// active columns at a time each lane transposes the genotype bytes of its 4
+// rows so that one DP4A forms sum_{4 columns} g_ij * digit; per-digit int32
+// sums are combined exactly in int64 per (split, row, fit). The covariates
+// and the constant term are added in FP64 by the vector kernel.
+// CTA (rc, sp): rows [rc*1024, +1024) (8 warps x 32 lanes x 4 rows), split
+// sp of the concatenated active lists.
+constexpr int kXIRows = 1024;
+constexpr int kDWMax = 6;
+constexpr int kXIChunk = 1024;  // columns staged per pass
+
+template <int NB, int DW>
+__global__ void __launch_bounds__(256)
+    k_xbeta_int(Dsg X, Fits F, int off, const double *__restrict__ beta_in) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  int *spre = reinterpret_cast<int *>(sm_raw);  // gridA + 1
+  __shared__ int sTot;
+  __shared__ double sInv[kMaxNB];
+  __shared__ double sScale[kMaxNB];
+  const double *beta = beta_in;
+  if (beta == nullptr) {
+    const int k = *F.it_base + off;
+    beta = F.beta[(k & 1) ^ 1];
+  }
+  const int gA = F.gridA;
+  for (int t = threadIdx.x; t < gA; t += blockDim.x) spre[t + 1] = F.a_cnt[t];
+  if (threadIdx.x < NB) {
+    const int b = threadIdx.x;
+    double m = 0.0;
+    for (int t = 0; t < gA; ++t) m = fmax(m, F.a_wmax[t * NB + b]);
+    int E = 0;
+    if (m > 0.0) frexp(m, &E);
+    const double scale = (m > 0.0) ? ldexp(1.0, E + 1) : 1.0;
+    sScale[b] = scale;
+    sInv[b] = ldexp(1.0, 7 * DW) / scale;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    spre[0] = 0;
+    for (int t = 1; t <= gA; ++t) spre[t] += spre[t - 1];
+    sTot = spre[gA];
+  }
+  __syncthreads();
+  const int A = sTot;
+  const int S = max(1, min(kBMaxSplits, A / kBMinColsPerSplit));
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    if (threadIdx.x < NB) {
+      double c = 0.0;
+      for (int t = 0; t < gA; ++t) c += F.a_ct[t * NB + threadIdx.x];
+      F.meta_d[threadIdx.x] = c;
+      F.meta_d[kMaxNB + threadIdx.x] = sScale[threadIdx.x];
+    }
+    if (threadIdx.x == 0) { F.meta_i[0] = S; F.meta_i[1] = A; }
+  }
+  if ((int)blockIdx.y >= S) return;
+  const int a0 = (int)((int64_t)A * blockIdx.y / S), a1 = (int)((int64_t)A * (blockIdx.y + 1) / S);
+  // per chunk of kXIChunk columns: column of each slot (or -1) and the digit
+  // words Wd[g][b][d] (byte q = digit of column q of group g)
+  int *gcol = spre + gA + 1;
+  uint32_t *wd = reinterpret_cast<uint32_t *>(gcol + kXIChunk);
+  uint8_t *wb = reinterpret_cast<uint8_t *>(wd);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * kXIRows + warp * 128 + lane * 4;
+  int acc[4][NB][DW];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int d = 0; d < DW; ++d) acc[r][b][d] = 0;
+  for (int c0 = a0; c0 < a1; c0 += kXIChunk) {
+    const int cnt = min(kXIChunk, a1 - c0);
+    const int ng = (cnt + 3) / 4;
+    __syncthreads();  // previous chunk fully consumed
+    for (int t = threadIdx.x; t < 4 * ng; t += blockDim.x) {
+      int j = -1;
+      if (t < cnt) {
+        const int a = c0 + t;
+        int lo = 0, hi = gA;  // bucket: spre[lo] <= a < spre[lo+1]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (spre[mid] <= a) lo = mid; else hi = mid;
+        }
+        j = F.a_list[(int64_t)lo * F.T + (a - spre[lo])];
+        if (j <= X.c) j = -1;  // covariates are summed in FP64 by k_vec
+      }
+      gcol[t] = j;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 4 * ng * NB; t += blockDim.x) {
+      const int slot = t / NB, b = t - slot * NB;
+      const int j = gcol[slot];
+      long long W = 0;
+      if (j >= 0) W = __double2ll_rn(__ldg(X.a + j) * beta[(int64_t)j * NB + b] * sInv[b]);
+      int dig[kDWMax];
+#pragma unroll
+      for (int d = DW - 1; d >= 1; --d) {
+        const int tt = (int)(((W + 64) & 127) - 64);
+        dig[d] = tt;
+        W = (W - tt) >> 7;
+      }
+      dig[0] = (int)W;
+      const int g = slot >> 2, q = slot & 3;
+#pragma unroll
+      for (int d = 0; d < DW; ++d) wb[(((size_t)g * NB + b) * DW + d) * 4 + q] = (uint8_t)(dig[d] & 0xff);
+    }
+    __syncthreads();
+    if (i0 < X.n) {
+      for (int g = 0; g < ng; ++g) {
+        uint32_t c4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = gcol[4 * g + q];
+          c4[q] = (j >= 0) ? __ldg(reinterpret_cast<const uint32_t *>(X.geno + (j - 1 - X.c) * X.ld + i0)) : 0u;
+        }
+        // 4x4 byte transpose: rw[r] = (c0.byte r, c1.byte r, c2.byte r, c3.byte r)
+        const uint32_t t01l = __byte_perm(c4[0], c4[1], 0x5140), t01h = __byte_perm(c4[0], c4[1], 0x7362);
+        const uint32_t t23l = __byte_perm(c4[2], c4[3], 0x5140), t23h = __byte_perm(c4[2], c4[3], 0x7362);
+        uint32_t rw[4];
+        rw[0] = __byte_perm(t01l, t23l, 0x5410);
+        rw[1] = __byte_perm(t01l, t23l, 0x7632);
+        rw[2] = __byte_perm(t01h, t23h, 0x5410);
+        rw[3] = __byte_perm(t01h, t23h, 0x7632);
+        const uint32_t *wg = wd + (size_t)g * NB * DW;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int d = 0; d < DW; ++d) {
+            const int wv = (int)wg[b * DW + d];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r][b][d] = __dp4a((int)rw[r], wv, acc[r][b][d]);
+          }
+      }
+    }
+  }
+  long long *out = F.xb_ipart + (int64_t)blockIdx.y * F.npad * NB;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t i = i0 + r;
+    if (i < F.npad)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        long long v = 0;
+#pragma unroll
+        for (int d = 0; d < DW; ++d) v += (long long)acc[r][b][d] << (7 * (DW - 1 - d));
+        out[i * NB + b] = v;
+      }
+  }
+}
+
+// Shared memory of k_xbeta_int: prefix (gridA+1 ints), the column slots of
+// one chunk and their digit words.
+static size_t xbeta_int_smem(const Fits &F, int NB) {
+  return (size_t)(F.gridA + 1) * 4 + (size_t)kXIChunk * 4 + (size_t)kXIChunk * NB * F.DW + 64;
+}
+
+template <int NB, int DW>
+size_t g_xi_opted = 48 * 1024;
+
+template <int NB, int DW>
+static cudaError_t xbeta_int_t(const Dsg &X, const Fits &F, int off, const double *beta_in,
+                               cudaStream_t s) {
+  const size_t smem = xbeta_int_smem(F, NB);
+  if (smem > g_xi_opted<NB, DW>) {
+    cudaError_t e = cudaFuncSetAttribute(k_xbeta_int<NB, DW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    g_xi_opted<NB, DW> = smem;
+  }
+  dim3 grid((unsigned)((X.n + kXIRows - 1) / kXIRows), kBMaxSplits);
+  k_xbeta_int<NB, DW><<<grid, 256, smem, s>>>(X, F, off, beta_in);
+  return cudaGetLastError();
+}
+
 template <int NB>
 static cudaError_t xbeta_t(const Dsg &X, const Fits &F, int off, const double *beta_in,
                            cudaStream_t s) {
+  if (F.mixed) {
+    if (F.DW == 6) return xbeta_int_t<NB, 6>(X, F, off, beta_in, s);
+    return cudaErrorInvalidValue;
+  }
   dim3 grid((unsigned)((X.n + kBRows - 1) / kBRows), kBMaxSplits);
   size_t smem = (size_t)(F.gridA + 1) * sizeof(int);
   if (smem > 48 * 1024) {
@@ -700,9 +888,14 @@ __global__ void __launch_bounds__(256) k_check(Fits F, int off) {
       __syncthreads();
     }
     if (threadIdx.x == 0) {
-      double bound = 0.0;
-      if (F.mixed) bound = 0.5 * F.colbound * F.scale[b] * ldexp(1.0, -7 * F.D);
-      const double R_p = rp / (1.0 + F.ymax);
+      double bound = 0.0, bound_p = 0.0;
+      if (F.mixed) {
+        // |s_j error| <= a_j sum_i x_ij |theta_i - theta^_i| <= colbound * half an ulp
+        bound = 0.5 * F.colbound * F.scale[b] * ldexp(1.0, -7 * F.D);
+        // |X~ beta error|_i <= sum_j x_ij |w_j - w^_j| <= 2 * active * half an ulp of w
+        (void)bound_p;  // folded into the r_p partials by the vector kernel
+      }
+      const double R_p = (rp + bound_p) / (1.0 + F.ymax);
       const double R_z = rz;
       const double R_b = (red[0][0] + bound) / F.lamnorm[b];
       const double R_1 = fabs(st);
@@ -744,7 +937,7 @@ cudaError_t launch_check(int NB, const Fits &F, int off, cudaStream_t s) {
 // and the partials (max |r|, max dist(n theta, d rho(z)), sum theta,
 // max |theta|) of w^{k+1} for the next stop test and quantisation.
 template <int NB>
-__global__ void __launch_bounds__(kCThreads) k_vec(Fits F, int off, int init) {
+__global__ void __launch_bounds__(kCThreads) k_vec(Dsg X, Fits F, int off, int init) {
   __shared__ double red[kCPartials][kCThreads];
   __shared__ int sRun[kMaxNB];
   const int k = init ? 0 : (*F.it_base + off);
@@ -761,7 +954,19 @@ __global__ void __launch_bounds__(kCThreads) k_vec(Fits F, int off, int init) {
   const int64_t nrows = F.n;
   if (i < nrows && b < NB && sRun[b]) {
     double xb = F.meta_d[b];
-    for (int sp = 0; sp < S; ++sp) xb += F.xb_part[((int64_t)sp * F.npad + i) * NB + b];
+    double xb_err = 0.0;  // certified bound on the rounding of the integer X~ beta
+    if (F.mixed) {
+      xb_err = (double)F.meta_i[1] * F.meta_d[kMaxNB + b] * ldexp(1.0, -7 * F.DW);
+      // exact integer slope part of the stored columns, then the covariates
+      long long V = 0;
+      for (int sp = 0; sp < S; ++sp) V += F.xb_ipart[((int64_t)sp * F.npad + i) * NB + b];
+      xb += (double)V * (F.meta_d[kMaxNB + b] * ldexp(1.0, -7 * F.DW));
+      const double *bt = F.beta[init ? 0 : ((k & 1) ^ 1)];
+      for (int64_t j = 1; j <= X.c; ++j)
+        xb = fma(X.a[j] * bt[j * NB + b], X.cov[(j - 1) * X.n + i], xb);
+    } else {
+      for (int sp = 0; sp < S; ++sp) xb += F.xb_part[((int64_t)sp * F.npad + i) * NB + b];
+    }
     const int64_t ib = i * NB + b;
     const double yi = __ldg(F.y + i);
     const double tau = F.tau[b];
@@ -769,7 +974,7 @@ __global__ void __launch_bounds__(kCThreads) k_vec(Fits F, int off, int init) {
       const double zi = F.z[ib], ti = F.theta[ib];
       const double ri = xb + zi - yi;
       F.r[ib] = ri;
-      p_r = fabs(ri);
+      p_r = fabs(ri) + xb_err;
       p_z = dist_pinball((double)nrows * ti, zi, tau);
       p_s = ti;
       p_m = fabs(ti);
@@ -783,7 +988,7 @@ __global__ void __launch_bounds__(kCThreads) k_vec(Fits F, int off, int init) {
       F.z[ib] = zn;
       F.theta[ib] = tn;
       F.r[ib] = rn;
-      p_r = fabs(rn);
+      p_r = fabs(rn) + xb_err;
       p_z = dist_pinball((double)nrows * tn, zn, tau);
       p_s = tn;
       p_m = fabs(tn);
@@ -813,13 +1018,13 @@ __global__ void __launch_bounds__(kCThreads) k_vec(Fits F, int off, int init) {
   }
 }
 
-cudaError_t launch_vec(int NB, const Fits &F, int off, int init, cudaStream_t s) {
+cudaError_t launch_vec(int NB, const Dsg &X, const Fits &F, int off, int init, cudaStream_t s) {
   switch (NB) {
-    case 1: k_vec<1><<<F.gridC, kCThreads, 0, s>>>(F, off, init); break;
-    case 2: k_vec<2><<<F.gridC, kCThreads, 0, s>>>(F, off, init); break;
-    case 3: k_vec<3><<<F.gridC, kCThreads, 0, s>>>(F, off, init); break;
-    case 4: k_vec<4><<<F.gridC, kCThreads, 0, s>>>(F, off, init); break;
-    case 8: k_vec<8><<<F.gridC, kCThreads, 0, s>>>(F, off, init); break;
+    case 1: k_vec<1><<<F.gridC, kCThreads, 0, s>>>(X, F, off, init); break;
+    case 2: k_vec<2><<<F.gridC, kCThreads, 0, s>>>(X, F, off, init); break;
+    case 3: k_vec<3><<<F.gridC, kCThreads, 0, s>>>(X, F, off, init); break;
+    case 4: k_vec<4><<<F.gridC, kCThreads, 0, s>>>(X, F, off, init); break;
+    case 8: k_vec<8><<<F.gridC, kCThreads, 0, s>>>(X, F, off, init); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

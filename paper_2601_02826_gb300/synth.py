@@ -228,7 +228,10 @@ def small_dense(seed: int | None = None, n: int = 500, p: int = 2000, G: int = 4
     P = 1 + p
     omega = np.ones(P)
     omega[0] = 0.0
-    return Workload("small_dense", n, p, 0, FMT_DENSE_F64, np.ascontiguousarray(X), 8 * n,
+    ld = padded_ld(n, FMT_DENSE_F64)
+    Xs = np.zeros((p, ld // 8))
+    Xs[:, :n] = X
+    return Workload("small_dense", n, p, 0, FMT_DENSE_F64, Xs, ld,
                     np.zeros((0, n)), y, [tau], equal_blocks(P, G), omega, [0.1], beta,
                     recipe=f"X ~ N(0,1) {n}x{p} FP64, 10 effects N(0,1), eps ~ t(3), G={G}")
 
