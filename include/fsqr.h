@@ -68,11 +68,15 @@ extern "C" {
                             codes 0/1/2, code 3 = missing */
 
 /* ---- arithmetic of the inner products ----------------------------------- */
-#define FSQR_FP64 0  /* plain FP64 for every product and reduction */
-#define FSQR_MIXED 1 /* X~^T theta from exact integer products: theta split into
-                        int8 digits, genotype x digit dot products accumulated
-                        exactly in int32 (DP4A); FP64 state, FP64 X~ beta and
-                        FP64 reductions. int8 storage only. */
+#define FSQR_FP64 0       /* plain FP64 for every product and reduction */
+#define FSQR_MIXED 1      /* exact integer products, FP64 state and reductions:
+                             X~^T theta on the tensor cores with theta split
+                             into base-16 digits (E4M3) against the genotype
+                             codes read as E4M3, FP32 accumulation that stays
+                             exact; X~ beta from int8 digits of a_j beta_j by
+                             DP4A with int64 sums. int8 storage only. */
+#define FSQR_MIXED_SIMT 2 /* as FSQR_MIXED, with X~^T theta from int8 digits of
+                             theta by DP4A on the SIMT cores instead */
 
 /* ---- starting point ------------------------------------------------------ */
 #define FSQR_WARM_NONE 0  /* beta = 0, z = y, theta = 0 */
@@ -109,7 +113,9 @@ typedef struct {
   double power_tol;       /* power-method relative change stop; default 1e-6 */
   int32_t precision;      /* FSQR_FP64 | FSQR_MIXED; default FSQR_FP64 */
   int32_t warm;           /* FSQR_WARM_*; default FSQR_WARM_NONE */
-  int32_t digits;         /* FSQR_MIXED: int8 digits per theta entry, 3..6; default 4 */
+  int32_t digits;         /* FSQR_MIXED_SIMT: int8 (7-bit) digits per theta entry, 3..5;
+                             FSQR_MIXED uses 7 base-16 digits (6 when digits == 3);
+                             default 4 */
   int32_t max_group;      /* fits advanced together per X pass, 1..8; default 4 */
   int64_t timeout_ms;     /* > 0: stop with FSQR_ETIMEOUT after this wall time */
 } fsqr_opts;

@@ -111,6 +111,35 @@ int pinned(fsqr_ctx *ctx, size_t count, double **out) {
 
 int64_t pad16(int64_t n) { return (n + 15) / 16 * 16; }
 
+// 2-D uint8 TMA descriptor with the 128-byte swizzle and zero fill outside
+// the tensor: dim0 contiguous (bytes), dim1 rows of stride1 bytes.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int make_tmap_u8(fsqr_ctx *ctx, CUtensorMap *out, const void *base, uint64_t dim0, uint64_t dim1,
+                 uint64_t stride1, uint32_t box0, uint32_t box1) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+      return fail(ctx, FSQR_ECUDA, "cuTensorMapEncodeTiled is not available");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  const cuuint64_t dims[2] = {dim0, dim1};
+  const cuuint64_t strides[1] = {stride1};
+  const cuuint32_t box[2] = {box0, box1};
+  const cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, FSQR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return FSQR_OK;
+}
+
 int64_t col_bytes(int64_t n, int fmt) {
   if (fmt == FSQR_DENSE_F64) return 8 * n;
   if (fmt == FSQR_INT8) return n;
@@ -359,11 +388,11 @@ int check_opts(fsqr_ctx *ctx, const fsqr_opts *o, int G) {
   if (!(o->tol >= 0.0)) return fail(ctx, FSQR_EINVAL, "tol must be >= 0");
   if (o->max_iter < 0) return fail(ctx, FSQR_EINVAL, "max_iter must be >= 0");
   if (o->check_every < 1) return fail(ctx, FSQR_EINVAL, "check_every must be >= 1");
-  if (o->precision != FSQR_FP64 && o->precision != FSQR_MIXED)
+  if (o->precision != FSQR_FP64 && o->precision != FSQR_MIXED && o->precision != FSQR_MIXED_SIMT)
     return fail(ctx, FSQR_EINVAL, "unknown precision %d", o->precision);
   if (o->warm < FSQR_WARM_NONE || o->warm > FSQR_WARM_PATH)
     return fail(ctx, FSQR_EINVAL, "unknown warm mode %d", o->warm);
-  if (o->precision == FSQR_MIXED && (o->digits < 3 || o->digits > 5))
+  if (o->precision != FSQR_FP64 && (o->digits < 3 || o->digits > 5))
     return fail(ctx, FSQR_EINVAL, "digits must be in 3..5");
   if (o->max_group < 1 || o->max_group > kMaxNB)
     return fail(ctx, FSQR_EINVAL, "max_group must be in 1..8");
@@ -403,7 +432,9 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   const int nb = gs.nb;
   const int NB = nb_template(nb);
   const int64_t n = X.n, npad = pad16(n), P = X.P;
-  const bool mixed = E.o->precision == FSQR_MIXED;
+  const bool mixed = E.o->precision == FSQR_MIXED || E.o->precision == FSQR_MIXED_SIMT;
+  // tensor-core column pass: int8 storage, at most 63 covariates, <= 4 fits
+  const bool tc = E.o->precision == FSQR_MIXED && X.fmt == FSQR_INT8 && X.p > 0 && X.c <= 63 && NB <= 4;
   const double t0 = now_ms();
   cudaStream_t st = ctx->stream;
 
@@ -429,12 +460,20 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   F.K = E.o->check_every;
   F.max_iter = E.o->max_iter;
   F.mixed = mixed ? 1 : 0;
-  F.D = mixed ? E.o->digits : 0;
+  F.D = mixed ? (tc ? (E.o->digits >= 4 ? 7 : 6) : E.o->digits) : 0;
+  F.dbits = tc ? 4 : 7;
   F.DW = mixed ? 6 : 0;
   F.n4p = npad / 4;
   F.colbound = E.pr->colbound;
   // tiling from the occupancy of the kernel this group runs
-  {
+  int tc_grid = 0, tc_tpc = 0;
+  if (tc) {
+    const int64_t tiles = (X.p + 127) / 128;
+    tc_grid = (int)std::min<int64_t>(tiles, ctx->num_sms);
+    tc_tpc = (int)((tiles + tc_grid - 1) / tc_grid);
+    F.T = 128 * tc_tpc;
+    F.gridA = tc_grid + 1;  // the last slot belongs to the dense columns
+  } else {
     Fits tmp = F;
     tmp.T = 32;
     size_t smem_est = col_pass_smem(A_PROX, tmp, NB) + 4096;
@@ -465,15 +504,32 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   int *it_base;
   TRY(wsget(ctx, "g_itbase", 1, &it_base));
   F.it_base = it_base;
+  uint8_t *dg = nullptr;
+  int *d_err = nullptr;
+  CUtensorMap tmX, tmD;
+  if (tc) {
+    const int N = tc_rows(NB, F.D);
+    TRY(wsget(ctx, "g_dg", (size_t)N * npad, &dg));
+    TRY(wsget(ctx, "g_err", 1, &d_err));
+    CK(cudaMemsetAsync(dg, 0, (size_t)N * npad, st));
+    CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    TRY(make_tmap_u8(ctx, &tmX, X.geno, (uint64_t)n, (uint64_t)X.p, (uint64_t)X.ld, 128, 128));
+    TRY(make_tmap_u8(ctx, &tmD, dg, (uint64_t)npad, (uint64_t)N, (uint64_t)npad, 128, (uint32_t)N));
+    const size_t smem = col_tc_smem(NB, F.D, F.T);
+    if (smem > 200 * 1024)
+      return fail(ctx, FSQR_EINVAL, "tensor-core column pass needs %zu B of shared memory", smem);
+  }
   if (mixed) {
-    TRY(wsget(ctx, "g_digits", (size_t)NB * F.D * F.n4p, &F.digits));
+    TRY(wsget(ctx, "g_digits", (size_t)NB * std::max(F.D, 1) * F.n4p, &F.digits));
     TRY(wsget(ctx, "g_scale", kMaxNB, &F.scale));
     TRY(wsget(ctx, "g_xbipart", (size_t)kBMaxSplits * npad * NB, &F.xb_ipart));
     TRY(wsget(ctx, "g_awmax", (size_t)F.gridA * NB, &F.a_wmax));
   }
-  const size_t smem = col_pass_smem(A_PROX, F, NB);
-  if (smem > 227 * 1024)
-    return fail(ctx, FSQR_EINVAL, "mixed group needs %zu B of shared memory (> 227 KB)", smem);
+  if (!tc) {
+    const size_t smem = col_pass_smem(A_PROX, F, NB);
+    if (smem > 227 * 1024)
+      return fail(ctx, FSQR_EINVAL, "mixed group needs %zu B of shared memory (> 227 KB)", smem);
+  }
 
   // ---- start point
   CK(cudaMemsetAsync(F.report, 0, sizeof(double) * kMaxNB * kReport, st));
@@ -509,16 +565,22 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   if (prof && !ctx->ev[0])
     for (int e = 0; e < 6; ++e) CK(cudaEventCreate(&ctx->ev[e]));
   int per_graph = 1;  // the advance kernel
-  for (int off = 0; off < M; ++off) per_graph += 3 + (mixed ? 1 : 0) + (off % K == 0 ? 1 : 0);
+  for (int off = 0; off < M; ++off) per_graph += 3 + (mixed ? 1 : 0) + (tc ? 1 : 0) + (off % K == 0 ? 1 : 0);
   // Enqueues steps base..base+M-1 (kernels read the base from it_base); with
   // sample set, events bracket the kernels of the second step.
   auto enqueue = [&](bool sample) -> cudaError_t {
     cudaError_t ce = cudaSuccess;
     for (int off = 0; off < M && ce == cudaSuccess; ++off) {
       const bool sm = sample && off == 1;
-      if (mixed) ce = launch_quantize(NB, F, off, st);
+      if (tc) ce = launch_quantize_tc(NB, F.D, F, off, dg, st);
+      else if (mixed) ce = launch_quantize(NB, F, off, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[0], st);
-      if (ce == cudaSuccess) ce = launch_col_pass(A_PROX, NB, X, F, off, nullptr, nullptr, nullptr, nullptr, st);
+      if (tc) {
+        if (ce == cudaSuccess) ce = launch_col_dense(NB, X, F, off, F.gridA - 1, st);
+        if (ce == cudaSuccess) ce = launch_col_tc(NB, F.D, X, F, off, tmX, tmD, tc_grid, tc_tpc, d_err, st);
+      } else if (ce == cudaSuccess) {
+        ce = launch_col_pass(A_PROX, NB, X, F, off, nullptr, nullptr, nullptr, nullptr, st);
+      }
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[1], st);
       if (ce == cudaSuccess) ce = launch_xbeta(NB, X, F, off, nullptr, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], st);
@@ -591,6 +653,13 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   }
   cudaGraphExecDestroy(exec);
   if (rc != FSQR_OK) return rc;
+  if (tc) {
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr != 0)
+      return fail(ctx, FSQR_ECUDA, "tensor-core column pass: a pipeline wait ran out of time (code %d)", herr);
+  }
   {
     // iterations actually taken by the live fits (done fits idle afterwards)
     int hd0[kMaxNB];
@@ -692,10 +761,10 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
   for (int t = 0; t < n_tau * n_lambda; ++t)
     if (!(lambdas[t] >= 0.0) || isinf(lambdas[t]))
       return fail(ctx, FSQR_EINVAL, "lambda must be finite and >= 0");
-  if (opts->precision == FSQR_MIXED && Xd && Xd->geno_format != FSQR_INT8)
-    return fail(ctx, FSQR_EINVAL, "FSQR_MIXED needs FSQR_INT8 genotype storage");
+  if (opts->precision != FSQR_FP64 && Xd && Xd->geno_format != FSQR_INT8)
+    return fail(ctx, FSQR_EINVAL, "mixed precision needs FSQR_INT8 genotype storage");
   Prep pr;
-  TRY(prepare(ctx, Xd, &pr, opts->precision == FSQR_MIXED));
+  TRY(prepare(ctx, Xd, &pr, opts->precision != FSQR_FP64));
   const Dsg &X = pr.X;
   const int64_t P = X.P, n = X.n;
   TRY(check_blocks(ctx, block_ptr, G, P));

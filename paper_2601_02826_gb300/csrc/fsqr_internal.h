@@ -1,6 +1,7 @@
 // Internal declarations shared by the FS-QRPPA kernels and the C-ABI layer.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -79,6 +80,7 @@ struct Fits {
   const int *it_base;
   // mixed precision
   int mixed, D;
+  int dbits;        // bits per digit of theta: 7 (int8 DP4A) or 4 (E4M3 tensor cores)
   int DW;           // digits of the X~ beta weights in the mixed path
   int64_t n4p;      // digit words per (fit, digit) row = npad / 4
   int32_t *digits;  // NB * D * n4p words, 4 samples per word
@@ -107,6 +109,15 @@ cudaError_t launch_vec(int NB, const Dsg &X, const Fits &F, int off, int init, c
 cudaError_t launch_advance(int *it_base, int M, cudaStream_t s);
 cudaError_t launch_gather_xb(int NB, const Fits &F, double *out, int64_t ldo, int nb,
                              cudaStream_t s);  // out[b*ldo + i], i < F.n (FP64 path)
+
+// Tensor-core column pass (k_tc.cu).
+cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, const CUtensorMap &tmX,
+                          const CUtensorMap &tmD, int grid, int tiles_per_cta, int *err,
+                          cudaStream_t s);
+cudaError_t launch_col_dense(int NB, const Dsg &X, const Fits &F, int off, int slot, cudaStream_t s);
+cudaError_t launch_quantize_tc(int NB, int D, const Fits &F, int off, uint8_t *dg, cudaStream_t s);
+size_t col_tc_smem(int NB, int D, int T);
+int tc_rows(int NB, int D);
 
 // Setup and reporting helpers (k_setup.cu).
 cudaError_t launch_vec_stats(const double *v, int64_t n, double *out3, cudaStream_t s);

@@ -891,7 +891,7 @@ __global__ void __launch_bounds__(256) k_check(Fits F, int off) {
       double bound = 0.0, bound_p = 0.0;
       if (F.mixed) {
         // |s_j error| <= a_j sum_i x_ij |theta_i - theta^_i| <= colbound * half an ulp
-        bound = 0.5 * F.colbound * F.scale[b] * ldexp(1.0, -7 * F.D);
+        bound = 0.5 * F.colbound * F.scale[b] * ldexp(1.0, -F.dbits * F.D);
         // |X~ beta error|_i <= sum_j x_ij |w_j - w^_j| <= 2 * active * half an ulp of w
         (void)bound_p;  // folded into the r_p partials by the vector kernel
       }

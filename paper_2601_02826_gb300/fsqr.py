@@ -17,7 +17,7 @@ from . import build as _build
 
 OK, EINVAL, ENOCONV, ETIMEOUT, ENUMERIC, ECUDA, ENOMEM = range(7)
 DENSE_F64, INT8, TWOBIT = 0, 1, 2
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_SIMT = 0, 1, 2
 WARM_NONE, WARM_GIVEN, WARM_PATH = 0, 1, 2
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOCONV", 3: "ETIMEOUT", 4: "ENUMERIC", 5: "ECUDA", 6: "ENOMEM"}

@@ -145,13 +145,15 @@ def test_fp64_converged_fit_matches_oracle(ctx, case, frac):
     assert info.active == int(np.sum(b[1:] != 0))
 
 
-@pytest.mark.parametrize("digits", [4, 5])
-def test_mixed_converged_fit_matches_oracle(ctx, digits):
+@pytest.mark.parametrize("precision,digits", [(1, 4), (2, 4), (2, 5)])
+def test_mixed_converged_fit_matches_oracle(ctx, precision, digits):
+    """precision 1: tensor-core digit products; 2: DP4A digit products."""
     w = CASES["int8"]()
     tau = w.taus[0]
     d, lmax, lam_s, lam, mu, bp, eta = oracle_problem(w, tau, 0.3)
     dw = _up(ctx, w)
-    rc, info, b, z, t = _run(ctx, dw, w, tau, lam_s, mu, eta, 200000, tol=1e-6, precision=1, digits=digits)
+    rc, info, b, z, t = _run(ctx, dw, w, tau, lam_s, mu, eta, 200000, tol=1e-6, precision=precision,
+                             digits=digits)
     assert rc == 0
     ref = O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=1e-6, max_iter=200000, lam_norm=lmax)
     ko = O.kkt(d.Xt, w.y, tau, lam, lmax, b, z, t)
@@ -160,13 +162,16 @@ def test_mixed_converged_fit_matches_oracle(ctx, digits):
     assert np.max(np.abs(b - ref.beta)) <= 1e-5
 
 
-def test_mixed_iterates_track_fp64(ctx):
-    """The digit products differ from FP64 only by the theta quantisation."""
-    w = CASES["int8"]()
+@pytest.mark.parametrize("case", ["int8", "rows"])
+@pytest.mark.parametrize("precision,digits", [(1, 4), (2, 5)])
+def test_mixed_iterates_track_fp64(ctx, case, precision, digits):
+    """The digit products differ from FP64 only by the theta quantisation
+    (2^-28 of max |theta| for 7 base-16 digits, 2^-35 for 5 int8 digits)."""
+    w = CASES[case]()
     tau = w.taus[0]
     d, lmax, lam_s, lam, mu, bp, eta = oracle_problem(w, tau, 0.2)
     dw = _up(ctx, w)
-    _, _, b, z, t = _run(ctx, dw, w, tau, lam_s, mu, eta, 50, precision=1, digits=5)
+    _, _, b, z, t = _run(ctx, dw, w, tau, lam_s, mu, eta, 50, precision=precision, digits=digits)
     ref = O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=0.0, max_iter=50)
     assert max_rel(b, ref.beta) <= 1e-7
     assert max_rel(t, ref.theta) <= 1e-7
@@ -185,7 +190,7 @@ def test_batch_grid_and_path_warm_start(ctx):
     lmaxs = [O.lambda_max(d.Xt, w.y, t, w.omega) for t in taus]
     lams = np.array([[f * lm for f in fr] for lm in lmaxs])
     B = len(taus) * len(fr)
-    for warm, prec in [(0, 0), (2, 0), (2, 1)]:
+    for warm, prec in [(0, 0), (2, 0), (2, 1), (0, 2)]:
         beta = torch.zeros(B * w.P, dtype=torch.float64, device="cuda")
         z = torch.zeros(B * w.n, dtype=torch.float64, device="cuda")
         th = torch.zeros(B * w.n, dtype=torch.float64, device="cuda")
