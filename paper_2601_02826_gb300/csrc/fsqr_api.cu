@@ -253,6 +253,20 @@ void col_tiling(fsqr_ctx *ctx, int64_t P, int per_sm, int *gridA, int *T) {
   *gridA = (int)((P + t - 1) / t);
 }
 
+// Totals, list prefix and last-CTA tickets of a pass (zeroed tickets).
+int alloc_totals(fsqr_ctx *ctx, Fits &F, const char *tag) {
+  std::string t(tag);
+  TRY(wsget(ctx, (t + "_totc0").c_str(), (size_t)kMaxNB * kCPartials, &F.tot_c[0]));
+  TRY(wsget(ctx, (t + "_totc1").c_str(), (size_t)kMaxNB * kCPartials, &F.tot_c[1]));
+  TRY(wsget(ctx, (t + "_tota").c_str(), (size_t)kMaxNB * 3, &F.tot_a));
+  TRY(wsget(ctx, (t + "_apre").c_str(), (size_t)F.gridA + 1, &F.a_pre));
+  TRY(wsget(ctx, (t + "_tick").c_str(), 2, &F.tickets));
+  CK(cudaMemsetAsync(F.tickets, 0, 2 * sizeof(unsigned), ctx->stream));
+  CK(cudaMemsetAsync(F.tot_c[0], 0, sizeof(double) * kMaxNB * kCPartials, ctx->stream));
+  CK(cudaMemsetAsync(F.tot_c[1], 0, sizeof(double) * kMaxNB * kCPartials, ctx->stream));
+  return FSQR_OK;
+}
+
 int nb_template(int nb) {
   if (nb <= 1) return 1;
   if (nb == 2) return 2;
@@ -463,6 +477,8 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   F.D = mixed ? (tc ? (E.o->digits >= 4 ? 7 : 6) : E.o->digits) : 0;
   F.dbits = tc ? 4 : 7;
   F.DW = mixed ? 6 : 0;
+  F.th_unit = ldexp(1.0, -F.dbits * F.D);
+  F.xb_unit = tc ? ldexp(1.0, -4 * 11) : ldexp(1.0, -7 * F.DW);
   F.n4p = npad / 4;
   F.colbound = E.pr->colbound;
   // tiling from the occupancy of the kernel this group runs
@@ -471,8 +487,8 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     const int64_t tiles = (X.p + 127) / 128;
     tc_grid = (int)std::min<int64_t>(tiles, ctx->num_sms);
     tc_tpc = (int)((tiles + tc_grid - 1) / tc_grid);
-    F.T = 128 * tc_tpc;
-    F.gridA = tc_grid + 1;  // the last slot belongs to the dense columns
+    F.T = 128 * tc_tpc + 64;  // tile columns, then up to 64 dense columns
+    F.gridA = tc_grid;
   } else {
     Fits tmp = F;
     tmp.T = 32;
@@ -483,7 +499,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
                   nb, smem_est);
     col_tiling(ctx, P, per_sm, &F.gridA, &F.T);
   }
-  F.gridC = (int)((n * NB + kCThreads - 1) / kCThreads);
+  F.gridC = (int)((n + kCThreads - 1) / kCThreads);  // row CTAs; the grid's y is the fit
   TRY(wsget(ctx, "g_beta0", (size_t)P * NB, &F.beta[0]));
   TRY(wsget(ctx, "g_beta1", (size_t)P * NB, &F.beta[1]));
   TRY(wsget(ctx, "g_z", (size_t)npad * NB, &F.z));
@@ -495,26 +511,36 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   TRY(wsget(ctx, "g_alist", (size_t)F.gridA * F.T, &F.a_list));
   TRY(wsget(ctx, "g_xbpart", (size_t)kBMaxSplits * npad * NB, &F.xb_part));
   TRY(wsget(ctx, "g_metai", 4, &F.meta_i));
-  TRY(wsget(ctx, "g_metad", kMaxNB, &F.meta_d));
+  TRY(wsget(ctx, "g_metad", 2 * kMaxNB, &F.meta_d));
   TRY(wsget(ctx, "g_cpart0", (size_t)F.gridC * NB * kCPartials, &F.c_part[0]));
   TRY(wsget(ctx, "g_cpart1", (size_t)F.gridC * NB * kCPartials, &F.c_part[1]));
+  TRY(alloc_totals(ctx, F, "g"));
   TRY(wsget(ctx, "g_done", kMaxNB, &F.done));
   TRY(wsget(ctx, "g_ndone", 1, &F.n_done));
   TRY(wsget(ctx, "g_report", (size_t)kMaxNB * kReport, &F.report));
   int *it_base;
   TRY(wsget(ctx, "g_itbase", 1, &it_base));
   F.it_base = it_base;
-  uint8_t *dg = nullptr;
-  int *d_err = nullptr;
-  CUtensorMap tmX, tmD;
+  uint8_t *dg = nullptr, *xt = nullptr, *wtile = nullptr;
+  int *d_err = nullptr, *scol = nullptr;
+  CUtensorMap tmG;
   if (tc) {
+    // tiled copy of X (byte image of the swizzled operand tiles) and the
+    // tiled digit matrix, one 128 x N block per 128-sample chunk
     const int N = tc_rows(NB, F.D);
-    TRY(wsget(ctx, "g_dg", (size_t)N * npad, &dg));
+    const int64_t nk = (n + 127) / 128;
+    const int64_t ntile = (X.p + 127) / 128;
+    TRY(wsget(ctx, "g_dgt", (size_t)(nk * N * 128), &dg));
+    TRY(wsget(ctx, "g_xt", (size_t)(ntile * nk * 16384), &xt));
     TRY(wsget(ctx, "g_err", 1, &d_err));
-    CK(cudaMemsetAsync(dg, 0, (size_t)N * npad, st));
+    CK(cudaMemsetAsync(dg, 0, (size_t)(nk * N * 128), st));
     CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-    TRY(make_tmap_u8(ctx, &tmX, X.geno, (uint64_t)n, (uint64_t)X.p, (uint64_t)X.ld, 128, 128));
-    TRY(make_tmap_u8(ctx, &tmD, dg, (uint64_t)npad, (uint64_t)N, (uint64_t)npad, 128, (uint32_t)N));
+    CK(launch_tile_x(X, xt, nk, st));
+    // rows of the stored matrix (one column each) for the gathered X~ beta
+    TRY(make_tmap_u8(ctx, &tmG, X.geno, (uint64_t)n, (uint64_t)X.p, (uint64_t)X.ld, 128, 1));
+    const int64_t maxkb = (P + 127) / 128;
+    TRY(wsget(ctx, "g_scol", (size_t)(maxkb * 128), &scol));
+    TRY(wsget(ctx, "g_wtile", (size_t)(maxkb * xbeta_tc_rows(NB) * 128), &wtile));
     const size_t smem = col_tc_smem(NB, F.D, F.T);
     if (smem > 200 * 1024)
       return fail(ctx, FSQR_EINVAL, "tensor-core column pass needs %zu B of shared memory", smem);
@@ -555,7 +581,8 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     }
   }
   CK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, F.beta[0], st));
-  CK(launch_xbeta(NB, X, F, 0, F.beta[0], st));
+  if (tc) CK(launch_xbeta_tc(NB, X, F, 0, F.beta[0], tmG, scol, wtile, d_err, st));
+  else CK(launch_xbeta(NB, X, F, 0, F.beta[0], st));
   CK(launch_vec(NB, X, F, 0, 1, st));
 
   // ---- the iteration as a captured graph of M steps
@@ -567,22 +594,23 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   int per_graph = 1;  // the advance kernel
   for (int off = 0; off < M; ++off) per_graph += 3 + (mixed ? 1 : 0) + (tc ? 1 : 0) + (off % K == 0 ? 1 : 0);
   // Enqueues steps base..base+M-1 (kernels read the base from it_base); with
-  // sample set, events bracket the kernels of the second step.
+  // sample set, events bracket the kernels of the last step.
   auto enqueue = [&](bool sample) -> cudaError_t {
     cudaError_t ce = cudaSuccess;
     for (int off = 0; off < M && ce == cudaSuccess; ++off) {
-      const bool sm = sample && off == 1;
+      const bool sm = sample && off == M - 1;
       if (tc) ce = launch_quantize_tc(NB, F.D, F, off, dg, st);
       else if (mixed) ce = launch_quantize(NB, F, off, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[0], st);
       if (tc) {
-        if (ce == cudaSuccess) ce = launch_col_dense(NB, X, F, off, F.gridA - 1, st);
-        if (ce == cudaSuccess) ce = launch_col_tc(NB, F.D, X, F, off, tmX, tmD, tc_grid, tc_tpc, d_err, st);
+        if (ce == cudaSuccess) ce = launch_col_tc(NB, F.D, X, F, off, xt, dg, tc_grid, tc_tpc, d_err, st);
       } else if (ce == cudaSuccess) {
         ce = launch_col_pass(A_PROX, NB, X, F, off, nullptr, nullptr, nullptr, nullptr, st);
       }
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[1], st);
-      if (ce == cudaSuccess) ce = launch_xbeta(NB, X, F, off, nullptr, st);
+      if (ce == cudaSuccess)
+        ce = tc ? launch_xbeta_tc(NB, X, F, off, nullptr, tmG, scol, wtile, d_err, st)
+                : launch_xbeta(NB, X, F, off, nullptr, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], st);
       if (off % K == 0 && ce == cudaSuccess) ce = launch_check(NB, F, off, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[3], st);
@@ -615,8 +643,8 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   int host_base = 0;
   int rc = FSQR_OK;
   for (int64_t l = 0;; ++l) {
-    // every 8th replay runs eagerly with events around one step's kernels
-    const bool sample = prof && (l % 8 == 0);
+    // every 4th replay runs eagerly with events around its last step's kernels
+    const bool sample = prof && (l % 4 == 0);
     ce = sample ? enqueue(true) : cudaGraphLaunch(exec, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(hdone, F.n_done, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
@@ -1084,7 +1112,8 @@ int fsqr_kkt(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, double tau, 
   TRY(wsget(ctx, "k_acnt", (size_t)F.gridA, &F.a_cnt));
   TRY(wsget(ctx, "k_alist", (size_t)F.gridA * F.T, &F.a_list));
   TRY(wsget(ctx, "k_metai", 4, &F.meta_i));
-  TRY(wsget(ctx, "k_metad", kMaxNB, &F.meta_d));
+  TRY(wsget(ctx, "k_metad", 2 * kMaxNB, &F.meta_d));
+  TRY(alloc_totals(ctx, F, "k"));
   int *done;
   TRY(wsget(ctx, "k_done", kMaxNB, &done));
   F.done = done;
@@ -1172,7 +1201,8 @@ int fsqr_predict(fsqr_ctx *ctx, const fsqr_design *Xd, const double *beta, int B
   TRY(wsget(ctx, "p_acnt", (size_t)F.gridA, &F.a_cnt));
   TRY(wsget(ctx, "p_alist", (size_t)F.gridA * F.T, &F.a_list));
   TRY(wsget(ctx, "p_metai", 4, &F.meta_i));
-  TRY(wsget(ctx, "p_metad", kMaxNB, &F.meta_d));
+  TRY(wsget(ctx, "p_metad", 2 * kMaxNB, &F.meta_d));
+  TRY(alloc_totals(ctx, F, "p"));
   int *done;
   TRY(wsget(ctx, "p_done", kMaxNB, &done));
   F.done = done;

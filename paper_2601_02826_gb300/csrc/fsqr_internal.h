@@ -18,7 +18,7 @@ constexpr int kBRowsPerThread = 8;
 constexpr int kBRows = kBThreads * kBRowsPerThread;
 constexpr int kBMaxSplits = 64;
 constexpr int kBMinColsPerSplit = 16;
-constexpr int kCThreads = 128;     // vector-update kernel
+constexpr int kCThreads = 32;      // vector-update kernel: one sample row per thread
 constexpr int kCPartials = 4;      // r_p max, r_z max, sum theta, max |theta|
 constexpr int kReport = 8;         // kkt, r_p, r_z, r_b, r_1, status, bound, iters
 
@@ -69,10 +69,15 @@ struct Fits {
   long long *xb_ipart;  // kBMaxSplits * npad * NB exact integer partials (mixed path)
   double *a_wmax;   // gridA*NB: max |a_j beta_j| over stored columns (mixed path)
   int *meta_i;      // [0] = splits used by the last X~ beta pass, [1] = active columns
-  double *meta_d;   // [0..NB) constant term, [kMaxNB..kMaxNB+NB) integer scale of the last pass
+  double *meta_d;   // 2*kMaxNB: [0..NB) constant term, [kMaxNB..kMaxNB+NB) integer scale of the last pass
   // vector-kernel partials of the iterate of each parity
   int gridC;
   double *c_part[2];  // gridC * NB * kCPartials
+  // totals reduced by the last CTA of each pass (fsqr_device.cuh)
+  double *tot_c[2];   // NB * kCPartials per parity
+  double *tot_a;      // NB * 3: max dist, constant term, max |a_j beta_j|
+  int *a_pre;         // gridA + 1: exclusive prefix of a_cnt
+  unsigned *tickets;  // [0] column pass, [1] vector kernel
   // per-fit status
   int *done;        // NB: iteration whose iterate is final, -1 while running
   int *n_done;      // counter of finished fits
@@ -82,6 +87,8 @@ struct Fits {
   int mixed, D;
   int dbits;        // bits per digit of theta: 7 (int8 DP4A) or 4 (E4M3 tensor cores)
   int DW;           // digits of the X~ beta weights in the mixed path
+  double th_unit;   // 2^(-dbits*D): the last digit's weight relative to the theta scale
+  double xb_unit;   // 2^(-7*DW): the same for the X~ beta weights
   int64_t n4p;      // digit words per (fit, digit) row = npad / 4
   int32_t *digits;  // NB * D * n4p words, 4 samples per word
   double *scale;    // NB: quantisation scale 2^e
@@ -111,10 +118,13 @@ cudaError_t launch_gather_xb(int NB, const Fits &F, double *out, int64_t ldo, in
                              cudaStream_t s);  // out[b*ldo + i], i < F.n (FP64 path)
 
 // Tensor-core column pass (k_tc.cu).
-cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, const CUtensorMap &tmX,
-                          const CUtensorMap &tmD, int grid, int tiles_per_cta, int *err,
+cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, const uint8_t *xt,
+                          const uint8_t *dgt, int grid, int tiles_per_cta, int *err,
                           cudaStream_t s);
-cudaError_t launch_col_dense(int NB, const Dsg &X, const Fits &F, int off, int slot, cudaStream_t s);
+cudaError_t launch_tile_x(const Dsg &X, uint8_t *xt, int64_t nk, cudaStream_t s);
+cudaError_t launch_xbeta_tc(int NB, const Dsg &X, const Fits &F, int off, const double *beta_in,
+                            const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err, cudaStream_t s);
+int xbeta_tc_rows(int NB);
 cudaError_t launch_quantize_tc(int NB, int D, const Fits &F, int off, uint8_t *dg, cudaStream_t s);
 size_t col_tc_smem(int NB, int D, int T);
 int tc_rows(int NB, int D);

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 
+#include "fsqr_device.cuh"
 #include "fsqr_internal.h"
 
 namespace fsqr {
@@ -264,8 +265,7 @@ __global__ void __launch_bounds__(kAThreads, ((D > 0 && NB * D <= 12) ? 2 : 1))
     const int b = threadIdx.x;
     double S = 0.0;
     if (MODE == A_PROX) {
-      const double *cp = F.c_part[k & 1];
-      for (int c = 0; c < F.gridC; ++c) S += cp[(c * NB + b) * kCPartials + 2];
+      S = F.tot_c[k & 1][b * kCPartials + 2];
       sIdle[b] = (b >= F.nb) || (F.done[b] >= 0);
       sScale[b] = D ? F.scale[b] : 1.0;
     } else if (MODE == A_XT) {
@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(kAThreads, ((D > 0 && NB * D <= 12) ? 2 : 1))
   for (int t = t0; t < t1; ++t)
     if (flags[t]) lst[pos++] = (int)(j0 + t);
   if (threadIdx.x == kAThreads - 1) F.a_cnt[blockIdx.x] = scan[kAThreads - 1];
+  col_finalize<NB>(F);
 }
 
 size_t col_pass_smem(int mode, const Fits &F, int NB) {
@@ -497,32 +498,20 @@ template <int NB>
 __global__ void __launch_bounds__(kBThreads)
     k_xbeta(Dsg X, Fits F, int off, const double *__restrict__ beta_in) {
   extern __shared__ int spre[];  // gridA + 1 prefix sums
-  __shared__ int sTot;
   const double *beta = beta_in;
   if (beta == nullptr) {
     const int k = *F.it_base + off;
     beta = F.beta[(k & 1) ^ 1];
   }
-  // exclusive prefix of the per-CTA counts (single-thread chunks, then serial)
+  // prefix of the per-CTA counts from the column pass's last CTA
   const int gA = F.gridA;
-  for (int t = threadIdx.x; t < gA; t += kBThreads) spre[t + 1] = F.a_cnt[t];
+  for (int t = threadIdx.x; t <= gA; t += kBThreads) spre[t] = __ldcg(F.a_pre + t);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    spre[0] = 0;
-    for (int t = 1; t <= gA; ++t) spre[t] += spre[t - 1];
-    sTot = spre[gA];
-  }
-  __syncthreads();
-  const int A = sTot;
+  const int A = spre[gA];
   const int S = max(1, min(kBMaxSplits, A / kBMinColsPerSplit));
   if (blockIdx.x == 0 && blockIdx.y == 0) {
-    // constant term of every fit, fixed summation order
-    if (threadIdx.x < NB) {
-      double c = 0.0;
-      for (int t = 0; t < gA; ++t) c += F.a_ct[t * NB + threadIdx.x];
-      F.meta_d[threadIdx.x] = c;
-    }
-    if (threadIdx.x == 0) F.meta_i[0] = S;
+    if (threadIdx.x < NB) F.meta_d[threadIdx.x] = F.tot_a[threadIdx.x * 3 + 1];
+    if (threadIdx.x == 0) { F.meta_i[0] = S; F.meta_i[1] = A; }
   }
   if ((int)blockIdx.y >= S) return;
   const int a0 = (int)((int64_t)A * blockIdx.y / S), a1 = (int)((int64_t)A * (blockIdx.y + 1) / S);
@@ -586,72 +575,59 @@ __global__ void __launch_bounds__(kBThreads)
 // Mixed path: exact integer X~ beta over the active stored columns.
 // w_jb = a_j beta_jb is rounded to a 7*DW-bit fixed-point integer W_jb with
 // the per-fit scale 2^(E_b+1) (max_j |w_jb| < 2^E_b over the stored active
-// columns, from the column pass), split into DW balanced int8 digits. For 4
-// active columns at a time each lane transposes the genotype bytes of its 4
-// rows so that one DP4A forms sum_{4 columns} g_ij * digit; per-digit int32
-// sums are combined exactly in int64 per (split, row, fit). The covariates
-// and the constant term are added in FP64 by the vector kernel.
-// CTA (rc, sp): rows [rc*1024, +1024) (8 warps x 32 lanes x 4 rows), split
-// sp of the concatenated active lists.
-constexpr int kXIRows = 1024;
+// columns, from the column pass's totals), split into DW balanced int8
+// digits. For 4 active columns at a time each thread gathers the genotype
+// bytes of its 2 rows and byte-transposes them so that one DP4A forms
+// sum_{4 columns} g_ij * digit; per-digit int32 sums are combined exactly in
+// int64 per (split, row, fit). The covariates and the constant term are
+// added in FP64 by the vector kernel.
+// CTA (rc, sp): rows [rc*512, +512) (256 threads x 2 rows), split sp of the
+// concatenated active lists, staged kXIChunk columns at a time.
+constexpr int kXIRows = 512;
 constexpr int kDWMax = 6;
-constexpr int kXIChunk = 1024;  // columns staged per pass
+constexpr int kXIChunk = 512;
+constexpr int kXIMaxSplits = 32;
 
 template <int NB, int DW>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_xbeta_int(Dsg X, Fits F, int off, const double *__restrict__ beta_in) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   int *spre = reinterpret_cast<int *>(sm_raw);  // gridA + 1
-  __shared__ int sTot;
   __shared__ double sInv[kMaxNB];
-  __shared__ double sScale[kMaxNB];
   const double *beta = beta_in;
   if (beta == nullptr) {
     const int k = *F.it_base + off;
     beta = F.beta[(k & 1) ^ 1];
   }
   const int gA = F.gridA;
-  for (int t = threadIdx.x; t < gA; t += blockDim.x) spre[t + 1] = F.a_cnt[t];
+  for (int t = threadIdx.x; t <= gA; t += blockDim.x) spre[t] = __ldcg(F.a_pre + t);
   if (threadIdx.x < NB) {
     const int b = threadIdx.x;
-    double m = 0.0;
-    for (int t = 0; t < gA; ++t) m = fmax(m, F.a_wmax[t * NB + b]);
+    const double m = F.tot_a[b * 3 + 2];
     int E = 0;
     if (m > 0.0) frexp(m, &E);
     const double scale = (m > 0.0) ? ldexp(1.0, E + 1) : 1.0;
-    sScale[b] = scale;
     sInv[b] = ldexp(1.0, 7 * DW) / scale;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    spre[0] = 0;
-    for (int t = 1; t <= gA; ++t) spre[t] += spre[t - 1];
-    sTot = spre[gA];
-  }
-  __syncthreads();
-  const int A = sTot;
-  const int S = max(1, min(kBMaxSplits, A / kBMinColsPerSplit));
-  if (blockIdx.x == 0 && blockIdx.y == 0) {
-    if (threadIdx.x < NB) {
-      double c = 0.0;
-      for (int t = 0; t < gA; ++t) c += F.a_ct[t * NB + threadIdx.x];
-      F.meta_d[threadIdx.x] = c;
-      F.meta_d[kMaxNB + threadIdx.x] = sScale[threadIdx.x];
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+      F.meta_d[b] = F.tot_a[b * 3 + 1];
+      F.meta_d[kMaxNB + b] = scale;
     }
-    if (threadIdx.x == 0) { F.meta_i[0] = S; F.meta_i[1] = A; }
   }
+  __syncthreads();
+  const int A = spre[gA];
+  const int S = max(1, min(kXIMaxSplits, A / kBMinColsPerSplit));
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) { F.meta_i[0] = S; F.meta_i[1] = A; }
   if ((int)blockIdx.y >= S) return;
   const int a0 = (int)((int64_t)A * blockIdx.y / S), a1 = (int)((int64_t)A * (blockIdx.y + 1) / S);
-  // per chunk of kXIChunk columns: column of each slot (or -1) and the digit
-  // words Wd[g][b][d] (byte q = digit of column q of group g)
+  // per chunk: column of each slot (or -1) and the digit words Wd[g][b][d]
+  // (byte q = digit of column q of group g)
   int *gcol = spre + gA + 1;
   uint32_t *wd = reinterpret_cast<uint32_t *>(gcol + kXIChunk);
   uint8_t *wb = reinterpret_cast<uint8_t *>(wd);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i0 = (int64_t)blockIdx.x * kXIRows + warp * 128 + lane * 4;
-  int acc[4][NB][DW];
+  const int64_t i0 = (int64_t)blockIdx.x * kXIRows + threadIdx.x * 2;
+  int acc[2][NB][DW];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -695,35 +671,30 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (i0 < X.n) {
       for (int g = 0; g < ng; ++g) {
-        uint32_t c4[4];
+        uint32_t c2[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = gcol[4 * g + q];
-          c4[q] = (j >= 0) ? __ldg(reinterpret_cast<const uint32_t *>(X.geno + (j - 1 - X.c) * X.ld + i0)) : 0u;
+          c2[q] = (j >= 0) ? (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(X.geno + (j - 1 - X.c) * X.ld + i0)) : 0u;
         }
-        // 4x4 byte transpose: rw[r] = (c0.byte r, c1.byte r, c2.byte r, c3.byte r)
-        const uint32_t t01l = __byte_perm(c4[0], c4[1], 0x5140), t01h = __byte_perm(c4[0], c4[1], 0x7362);
-        const uint32_t t23l = __byte_perm(c4[2], c4[3], 0x5140), t23h = __byte_perm(c4[2], c4[3], 0x7362);
-        uint32_t rw[4];
-        rw[0] = __byte_perm(t01l, t23l, 0x5410);
-        rw[1] = __byte_perm(t01l, t23l, 0x7632);
-        rw[2] = __byte_perm(t01h, t23h, 0x5410);
-        rw[3] = __byte_perm(t01h, t23h, 0x7632);
+        // rows i0, i0+1 as (column 0..3) byte vectors
+        const uint32_t x01 = c2[0] | (c2[1] << 16), x23 = c2[2] | (c2[3] << 16);
+        const uint32_t rw0 = __byte_perm(x01, x23, 0x6420), rw1 = __byte_perm(x01, x23, 0x7531);
         const uint32_t *wg = wd + (size_t)g * NB * DW;
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
           for (int d = 0; d < DW; ++d) {
             const int wv = (int)wg[b * DW + d];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[r][b][d] = __dp4a((int)rw[r], wv, acc[r][b][d]);
+            acc[0][b][d] = __dp4a((int)rw0, wv, acc[0][b][d]);
+            acc[1][b][d] = __dp4a((int)rw1, wv, acc[1][b][d]);
           }
       }
     }
   }
   long long *out = F.xb_ipart + (int64_t)blockIdx.y * F.npad * NB;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < 2; ++r) {
     const int64_t i = i0 + r;
     if (i < F.npad)
 #pragma unroll
@@ -754,7 +725,7 @@ static cudaError_t xbeta_int_t(const Dsg &X, const Fits &F, int off, const doubl
     if (e != cudaSuccess) return e;
     g_xi_opted<NB, DW> = smem;
   }
-  dim3 grid((unsigned)((X.n + kXIRows - 1) / kXIRows), kBMaxSplits);
+  dim3 grid((unsigned)((X.n + kXIRows - 1) / kXIRows), kXIMaxSplits);
   k_xbeta_int<NB, DW><<<grid, 256, smem, s>>>(X, F, off, beta_in);
   return cudaGetLastError();
 }
@@ -800,9 +771,7 @@ __global__ void __launch_bounds__(256) k_quantize(Fits F, int off) {
   __shared__ double sInv[kMaxNB];
   if (threadIdx.x < NB) {
     const int b = threadIdx.x;
-    const double *cp = F.c_part[k & 1];
-    double m = 0.0;
-    for (int c = 0; c < F.gridC; ++c) m = fmax(m, cp[(c * NB + b) * kCPartials + 3]);
+    const double m = F.tot_c[k & 1][b * kCPartials + 3];
     int E = 0;
     if (m > 0.0) frexp(m, &E);  // m = f 2^E, f in [0.5, 1)
     const double scale = (m > 0.0) ? ldexp(1.0, E + 1) : 1.0;
@@ -866,62 +835,42 @@ cudaError_t launch_quantize(int NB, const Fits &F, int off, cudaStream_t s) {
 // combines the column pass's R_b partials with the vector kernel's partials
 // of w^k. A fit stops when KKT <= tol, when k >= max_iter, or on NaN.
 template <int NB>
-__global__ void __launch_bounds__(256) k_check(Fits F, int off) {
+__global__ void __launch_bounds__(32) k_check(Fits F, int off) {
   const int k = *F.it_base + off;
-  __shared__ double red[4][256];
-  for (int b = 0; b < F.nb; ++b) {
-    if (F.done[b] >= 0) continue;  // uniform across the CTA
-    double rb = 0.0, rp = 0.0, rz = 0.0, st = 0.0;
-    for (int c = threadIdx.x; c < F.gridA; c += blockDim.x) rb = fmax(rb, F.a_rb[c * NB + b]);
-    const double *cp = F.c_part[k & 1];
-    if (threadIdx.x == 0) {
-      for (int c = 0; c < F.gridC; ++c) {
-        rp = fmax(rp, cp[(c * NB + b) * kCPartials + 0]);
-        rz = fmax(rz, cp[(c * NB + b) * kCPartials + 1]);
-        st += cp[(c * NB + b) * kCPartials + 2];
-      }
-    }
-    red[0][threadIdx.x] = rb;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o; o >>= 1) {
-      if (threadIdx.x < (unsigned)o) red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + o]);
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      double bound = 0.0, bound_p = 0.0;
-      if (F.mixed) {
-        // |s_j error| <= a_j sum_i x_ij |theta_i - theta^_i| <= colbound * half an ulp
-        bound = 0.5 * F.colbound * F.scale[b] * ldexp(1.0, -F.dbits * F.D);
-        // |X~ beta error|_i <= sum_j x_ij |w_j - w^_j| <= 2 * active * half an ulp of w
-        (void)bound_p;  // folded into the r_p partials by the vector kernel
-      }
-      const double R_p = (rp + bound_p) / (1.0 + F.ymax);
-      const double R_z = rz;
-      const double R_b = (red[0][0] + bound) / F.lamnorm[b];
-      const double R_1 = fabs(st);
-      const double kkt = fmax(fmax(R_p, R_z), fmax(R_b, R_1));
-      const bool bad = !(kkt == kkt) || isinf(kkt);
-      double *rep = F.report + b * kReport;
-      rep[0] = kkt; rep[1] = R_p; rep[2] = R_z; rep[3] = R_b; rep[4] = R_1;
-      rep[6] = bound / F.lamnorm[b];
-      rep[7] = k;
-      if (bad || kkt <= F.tol || k >= F.max_iter) {
-        rep[5] = bad ? FSQR_ENUMERIC : (kkt <= F.tol ? FSQR_OK : FSQR_ENOCONV);
-        F.done[b] = k;
-        atomicAdd(F.n_done, 1);
-      }
-    }
-    __syncthreads();
+  const int b = threadIdx.x;
+  if (b >= F.nb || F.done[b] >= 0) return;
+  const double *tc = F.tot_c[k & 1] + b * kCPartials;
+  const double rb = F.tot_a[b * 3 + 0];
+  double bound = 0.0;
+  if (F.mixed) {
+    // |s_j error| <= a_j sum_i x_ij |theta_i - theta^_i| <= colbound * half an ulp;
+    // the X~ beta rounding bound is already inside the r_p partials
+    bound = 0.5 * F.colbound * F.scale[b] * F.th_unit;
+  }
+  const double R_p = tc[0] / (1.0 + F.ymax);
+  const double R_z = tc[1];
+  const double R_b = (rb + bound) / F.lamnorm[b];
+  const double R_1 = fabs(tc[2]);
+  const double kkt = fmax(fmax(R_p, R_z), fmax(R_b, R_1));
+  const bool bad = !(kkt == kkt) || isinf(kkt);
+  double *rep = F.report + b * kReport;
+  rep[0] = kkt; rep[1] = R_p; rep[2] = R_z; rep[3] = R_b; rep[4] = R_1;
+  rep[6] = bound / F.lamnorm[b];
+  rep[7] = k;
+  if (bad || kkt <= F.tol || k >= F.max_iter) {
+    rep[5] = bad ? FSQR_ENUMERIC : (kkt <= F.tol ? FSQR_OK : FSQR_ENOCONV);
+    F.done[b] = k;
+    atomicAdd(F.n_done, 1);
   }
 }
 
 cudaError_t launch_check(int NB, const Fits &F, int off, cudaStream_t s) {
   switch (NB) {
-    case 1: k_check<1><<<1, 256, 0, s>>>(F, off); break;
-    case 2: k_check<2><<<1, 256, 0, s>>>(F, off); break;
-    case 3: k_check<3><<<1, 256, 0, s>>>(F, off); break;
-    case 4: k_check<4><<<1, 256, 0, s>>>(F, off); break;
-    case 8: k_check<8><<<1, 256, 0, s>>>(F, off); break;
+    case 1: k_check<1><<<1, 32, 0, s>>>(F, off); break;
+    case 2: k_check<2><<<1, 32, 0, s>>>(F, off); break;
+    case 3: k_check<3><<<1, 32, 0, s>>>(F, off); break;
+    case 4: k_check<4><<<1, 32, 0, s>>>(F, off); break;
+    case 8: k_check<8><<<1, 32, 0, s>>>(F, off); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -938,93 +887,122 @@ cudaError_t launch_check(int NB, const Fits &F, int off, cudaStream_t s) {
 // max |theta|) of w^{k+1} for the next stop test and quantisation.
 template <int NB>
 __global__ void __launch_bounds__(kCThreads) k_vec(Dsg X, Fits F, int off, int init) {
-  __shared__ double red[kCPartials][kCThreads];
-  __shared__ int sRun[kMaxNB];
+  __shared__ double red[kCPartials][256];
   const int k = init ? 0 : (*F.it_base + off);
-  if (threadIdx.x < NB) {
-    const int b = threadIdx.x;
-    sRun[b] = (b < F.nb) && (init || F.done[b] < 0);
-  }
-  __syncthreads();
-  const int64_t g = (int64_t)blockIdx.x * kCThreads + threadIdx.x;
-  const int64_t i = g / NB;
-  const int b = (int)(g - i * NB);
-  double p_r = 0.0, p_z = 0.0, p_s = 0.0, p_m = 0.0;
+  const int64_t i = (int64_t)blockIdx.x * kCThreads + threadIdx.x;
   const int S = F.meta_i[0];
   const int64_t nrows = F.n;
-  if (i < nrows && b < NB && sRun[b]) {
-    double xb = F.meta_d[b];
-    double xb_err = 0.0;  // certified bound on the rounding of the integer X~ beta
+  const bool row = i < nrows;
+  double p[NB][kCPartials];
+  bool run[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    run[b] = (b < F.nb) && (init || F.done[b] < 0);
+#pragma unroll
+    for (int q = 0; q < kCPartials; ++q) p[b][q] = 0.0;
+  }
+  if (row) {
+    double xb[NB], xb_err[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) { xb[b] = F.meta_d[b]; xb_err[b] = 0.0; }
     if (F.mixed) {
-      xb_err = (double)F.meta_i[1] * F.meta_d[kMaxNB + b] * ldexp(1.0, -7 * F.DW);
       // exact integer slope part of the stored columns, then the covariates
-      long long V = 0;
-      for (int sp = 0; sp < S; ++sp) V += F.xb_ipart[((int64_t)sp * F.npad + i) * NB + b];
-      xb += (double)V * (F.meta_d[kMaxNB + b] * ldexp(1.0, -7 * F.DW));
+      long long V[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) V[b] = 0;
+      // all split partials are loaded before any is added (no serial latency)
+      for (int sp0 = 0; sp0 < S; sp0 += 8) {
+        long long v[8][NB];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const long long *src = F.xb_ipart + ((int64_t)(sp0 + u) * F.npad + i) * NB;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) v[u][b] = (sp0 + u < S) ? __ldcg(src + b) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) V[b] += v[u][b];
+      }
       const double *bt = F.beta[init ? 0 : ((k & 1) ^ 1)];
-      for (int64_t j = 1; j <= X.c; ++j)
-        xb = fma(X.a[j] * bt[j * NB + b], X.cov[(j - 1) * X.n + i], xb);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const double unit = F.meta_d[kMaxNB + b] * F.xb_unit;
+        xb_err[b] = (double)F.meta_i[1] * unit;
+        xb[b] += (double)V[b] * unit;
+      }
+#pragma unroll 4
+      for (int64_t j = 1; j <= X.c; ++j) {
+        const double x = __ldg(X.cov + (j - 1) * X.n + i), aj = __ldg(X.a + j);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) xb[b] = fma(aj * __ldg(bt + j * NB + b), x, xb[b]);
+      }
     } else {
-      for (int sp = 0; sp < S; ++sp) xb += F.xb_part[((int64_t)sp * F.npad + i) * NB + b];
+#pragma unroll 8
+      for (int sp = 0; sp < S; ++sp) {
+        const double *src = F.xb_part + ((int64_t)sp * F.npad + i) * NB;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) xb[b] += __ldcg(src + b);
+      }
     }
-    const int64_t ib = i * NB + b;
     const double yi = __ldg(F.y + i);
-    const double tau = F.tau[b];
-    if (init) {
-      const double zi = F.z[ib], ti = F.theta[ib];
-      const double ri = xb + zi - yi;
-      F.r[ib] = ri;
-      p_r = fabs(ri) + xb_err;
-      p_z = dist_pinball((double)nrows * ti, zi, tau);
-      p_s = ti;
-      p_m = fabs(ti);
-    } else {
-      const double zo = F.z[ib], th = F.theta[ib], ro = F.r[ib];
-      const double nmu = (double)nrows * F.mu;
-      const double v = zo + th / F.mu;
-      const double zn = fmax(v - tau / nmu, 0.0) - fmax(-v - (1.0 - tau) / nmu, 0.0);
-      const double rn = xb + zn - yi;
-      const double tn = th - F.sigma * (2.0 * rn - ro);
-      F.z[ib] = zn;
-      F.theta[ib] = tn;
-      F.r[ib] = rn;
-      p_r = fabs(rn) + xb_err;
-      p_z = dist_pinball((double)nrows * tn, zn, tau);
-      p_s = tn;
-      p_m = fabs(tn);
+    const double nmu = (double)nrows * F.mu;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (!run[b]) continue;
+      const int64_t ib = i * NB + b;
+      const double tau = F.tau[b];
+      if (init) {
+        const double zi = F.z[ib], ti = F.theta[ib];
+        const double ri = xb[b] + zi - yi;
+        F.r[ib] = ri;
+        p[b][0] = fabs(ri) + xb_err[b];
+        p[b][1] = dist_pinball((double)nrows * ti, zi, tau);
+        p[b][2] = ti;
+        p[b][3] = fabs(ti);
+      } else {
+        const double zo = F.z[ib], th = F.theta[ib], ro = F.r[ib];
+        const double v = zo + th / F.mu;
+        // eq. z_update
+        const double zn = fmax(v - tau / nmu, 0.0) - fmax(-v - (1.0 - tau) / nmu, 0.0);
+        // eq. fsppa_update, theta line: extrapolated dual step of size mu/(G+1)
+        const double rn = xb[b] + zn - yi;
+        const double tn = th - F.sigma * (2.0 * rn - ro);
+        F.z[ib] = zn;
+        F.theta[ib] = tn;
+        F.r[ib] = rn;
+        p[b][0] = fabs(rn) + xb_err[b];
+        p[b][1] = dist_pinball((double)nrows * tn, zn, tau);
+        p[b][2] = tn;
+        p[b][3] = fabs(tn);
+      }
     }
   }
-  red[0][threadIdx.x] = p_r;
-  red[1][threadIdx.x] = p_z;
-  red[2][threadIdx.x] = p_s;
-  red[3][threadIdx.x] = p_m;
-  __syncthreads();
-  if (threadIdx.x < NB) {
-    const int bb = threadIdx.x;
-    const int par = init ? 0 : ((k + 1) & 1);
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    for (int t = 0; t < kCThreads; ++t) {
-      const int64_t gt = (int64_t)blockIdx.x * kCThreads + t;
-      if ((int)(gt % NB) != bb) continue;
-      a0 = fmax(a0, red[0][t]);
-      a1 = fmax(a1, red[1][t]);
-      a2 += red[2][t];
-      a3 = fmax(a3, red[3][t]);
+  const int par = init ? 0 : ((k + 1) & 1);
+  const int ops[4] = {0, 0, 1, 0};
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+#pragma unroll
+    for (int q = 0; q < kCPartials; ++q) red[q][threadIdx.x] = p[b][q];
+    __syncthreads();
+    tree_reduce<4>(red, ops, kCThreads);
+    if (threadIdx.x == 0 && run[b]) {
+      double *cp = F.c_part[par] + (blockIdx.x * NB + b) * kCPartials;
+      cp[0] = red[0][0]; cp[1] = red[1][0]; cp[2] = red[2][0]; cp[3] = red[3][0];
     }
-    if (sRun[bb]) {
-      double *cp = F.c_part[par] + (blockIdx.x * NB + bb) * kCPartials;
-      cp[0] = a0; cp[1] = a1; cp[2] = a2; cp[3] = a3;
-    }
+    __syncthreads();
   }
+  vec_finalize<NB>(F, par);
 }
 
 cudaError_t launch_vec(int NB, const Dsg &X, const Fits &F, int off, int init, cudaStream_t s) {
+  const unsigned grid = (unsigned)F.gridC;
   switch (NB) {
-    case 1: k_vec<1><<<F.gridC, kCThreads, 0, s>>>(X, F, off, init); break;
-    case 2: k_vec<2><<<F.gridC, kCThreads, 0, s>>>(X, F, off, init); break;
-    case 3: k_vec<3><<<F.gridC, kCThreads, 0, s>>>(X, F, off, init); break;
-    case 4: k_vec<4><<<F.gridC, kCThreads, 0, s>>>(X, F, off, init); break;
-    case 8: k_vec<8><<<F.gridC, kCThreads, 0, s>>>(X, F, off, init); break;
+    case 1: k_vec<1><<<grid, kCThreads, 0, s>>>(X, F, off, init); break;
+    case 2: k_vec<2><<<grid, kCThreads, 0, s>>>(X, F, off, init); break;
+    case 3: k_vec<3><<<grid, kCThreads, 0, s>>>(X, F, off, init); break;
+    case 4: k_vec<4><<<grid, kCThreads, 0, s>>>(X, F, off, init); break;
+    case 8: k_vec<8><<<grid, kCThreads, 0, s>>>(X, F, off, init); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -6,8 +6,11 @@
 //     balanced base-16 digits t in [-8, 8]; every digit is an exact E4M3
 //     value. The digits of the NB fits form an N x n matrix (rows b*D + d).
 //   * The int8 genotype codes 0/1/2 read as E4M3 bit patterns are the
-//     subnormals 0, 2^-9, 2^-8, i.e. exactly g * 2^-9, so the stored
-//     matrix is loaded by TMA and multiplied with no conversion pass.
+//     subnormals 0, 2^-9, 2^-8, i.e. exactly g * 2^-9, so the codes are
+//     multiplied with no conversion. Before the iteration the stored matrix
+//     is copied once into tiles of 128 columns x 128 samples laid out as
+//     the byte image of the swizzled shared-memory operand (k_tile_x), so
+//     every stage is one contiguous 16 KB bulk copy.
 //   * tcgen05.mma kind::f8f6f4 (M = 128 columns, N = digit rows, K = 32
 //     samples) accumulates g * t * 2^-9 in FP32 in tensor memory; every
 //     partial sum is an integer multiple of 2^-9 below 2^24 * 2^-9, hence
@@ -15,14 +18,18 @@
 // The FP64 proximal update (eq. beta_update), the stop-test distance and the
 // active-column lists follow as in the SIMT column pass.
 //
-// Roles (192 threads): warp 0 issues TMA loads into a STAGES-deep ring,
+// Roles (256 threads): warp 0 issues TMA loads into a STAGES-deep ring,
 // warp 1 issues the MMAs (one elected thread) into a double-buffered TMEM
-// accumulator, warps 2-5 (128 threads, one per tile row) run the epilogue.
-// CTA c takes the 128-column tiles c, c + grid, c + 2 grid, ...
+// accumulator, warps 2-5 (128 threads, one per tile row) run the epilogue,
+// warps 6-7 handle the FP64 dense columns (intercept, covariates) j =
+// blockIdx.x, blockIdx.x + grid, ... <= c. CTA c takes the 128-column tiles
+// c, c + grid, c + 2 grid, ... Its active list holds its tile columns in
+// tile order, then its dense columns.
 #include <cuda.h>
 #include <math.h>
 #include <stdint.h>
 
+#include "fsqr_device.cuh"
 #include "fsqr_internal.h"
 #include "sm103_ops.cuh"
 
@@ -30,16 +37,21 @@ namespace fsqr {
 
 using namespace sm103;
 
+// E4M3 encodings of the integers -8..8 (index t + 8).
+__constant__ uint8_t kE4M3Int[17] = {0xD0, 0xCE, 0xCC, 0xCA, 0xC8, 0xC4, 0xC0, 0xB8, 0x00,
+                                     0x38, 0x40, 0x44, 0x48, 0x4A, 0x4C, 0x4E, 0x50};
+
 template <int NB, int D>
 struct TcShape {
   static constexpr int NR = NB * D;
   static constexpr int N = NR <= 16 ? 16 : (NR <= 32 ? 32 : 64);
-  static constexpr int TMEM_COLS = (2 * N <= 32) ? 32 : ((2 * N <= 64) ? 64 : 128);
+  static constexpr int ACC = 4;  // TMEM accumulator buffers
+  static constexpr int TMEM_COLS = (ACC * N <= 32) ? 32 : ((ACC * N <= 64) ? 64 : ((ACC * N <= 128) ? 128 : 256));
   static constexpr int STAGES = 6;
   static constexpr int A_BYTES = 128 * 128;
   static constexpr int B_BYTES = N * 128;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int THREADS = 192;
+  static constexpr int THREADS = 256;
 };
 
 __device__ __forceinline__ double dist_l1_tc(double s, double lam, double b) {
@@ -58,25 +70,29 @@ __device__ __forceinline__ int block_of_tc(const int64_t *__restrict__ bp, int G
 }
 
 template <int NB, int D>
-__global__ void __launch_bounds__(192, 1)
-    k_col_tc(Dsg X, Fits F, int off, const __grid_constant__ CUtensorMap tmX,
-             const __grid_constant__ CUtensorMap tmD, int tiles_per_cta, int *err) {
+__global__ void __launch_bounds__(256, 1)
+    k_col_tc(Dsg X, Fits F, int off, const uint8_t *__restrict__ xt, const uint8_t *__restrict__ dgt,
+             int tiles_per_cta, int *err) {
   using Sh = TcShape<NB, D>;
   constexpr int N = Sh::N;
   constexpr int S = Sh::STAGES;
+  constexpr int kAcc = Sh::ACC;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[S], empty[S], accf[2], acce[2], drain;
+  __shared__ __align__(8) uint64_t full[S], empty[S], accf[kAcc], acce[kAcc], drain;
   __shared__ uint32_t tmem_base;
   __shared__ double sS[kMaxNB], sScale[kMaxNB];
   __shared__ int sIdle[kMaxNB];
-  __shared__ double red_rb[128][NB], red_ct[128][NB], red_wm[128][NB];
+  __shared__ double red[3][256];
   __shared__ int scan[Sh::THREADS];
+  __shared__ int s_dense_act[64];
+  __shared__ int s_ndense;
 
   // 1024-aligned ring of stages, then the active flags of this CTA's columns
   const uint32_t base_u32 = smem_u32(smem_raw);
   uint8_t *ring = smem_raw + (((base_u32 + 1023u) & ~1023u) - base_u32);
   uint8_t *flags = ring + S * Sh::STAGE_BYTES;
-  const int T = F.T;  // = 128 * tiles_per_cta
+  const int T = F.T;                       // list stride: 128 * tiles_per_cta + 64
+  const int TF = 128 * tiles_per_cta;      // flags of the tile columns
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = *F.it_base + off;
@@ -88,29 +104,27 @@ __global__ void __launch_bounds__(192, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int a = 0; a < 2; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], 128); }
+    for (int a = 0; a < kAcc; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], 128); }
     mbar_init(&drain, 1);
     fence_mbar_init();
   }
   if (threadIdx.x < NB) {
     const int b = threadIdx.x;
-    const double *cp = F.c_part[k & 1];
-    double Ssum = 0.0;
-    for (int c = 0; c < F.gridC; ++c) Ssum += cp[(c * NB + b) * kCPartials + 2];
-    sS[b] = Ssum;
+    sS[b] = F.tot_c[k & 1][b * kCPartials + 2];
     sIdle[b] = (b >= F.nb) || (F.done[b] >= 0);
     sScale[b] = F.scale[b];
   }
-  for (int t = threadIdx.x; t < T; t += Sh::THREADS) flags[t] = 0;
-  if (warp == 0 && lane == 0) {
-    prefetch_tmap(&tmX);
-    prefetch_tmap(&tmD);
-  }
+  if (threadIdx.x == 0) s_ndense = 0;
+  for (int t = threadIdx.x; t < TF; t += Sh::THREADS) flags[t] = 0;
   if (warp == 1) tmem_alloc(&tmem_base, Sh::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
+  // per-thread partials (max dist, constant term, max |a_j beta_j|)
+  double rbl[NB], ctl[NB], wml[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) { rbl[b] = 0.0; ctl[b] = 0.0; wml[b] = 0.0; }
 
   if (warp == 0) {
     // ---------------------------------------------------------- TMA producer
@@ -124,8 +138,8 @@ __global__ void __launch_bounds__(192, 1)
           if (!mbar_wait(&empty[s], ph ^ 1u, err, kErrEmpty)) goto producer_done;
           uint8_t *sa = ring + s * Sh::STAGE_BYTES;
           mbar_arrive_expect_tx(&full[s], Sh::STAGE_BYTES);
-          tma_load_2d(sa, &tmX, &full[s], kc * 128, tile * 128);
-          tma_load_2d(sa + Sh::A_BYTES, &tmD, &full[s], kc * 128, 0);
+          bulk_load(sa, xt + ((int64_t)tile * nk + kc) * Sh::A_BYTES, Sh::A_BYTES, &full[s]);
+          bulk_load(sa + Sh::A_BYTES, dgt + (int64_t)kc * Sh::B_BYTES, Sh::B_BYTES, &full[s]);
         }
       }
     producer_done:;
@@ -136,8 +150,8 @@ __global__ void __launch_bounds__(192, 1)
       const uint32_t idesc = idesc_f32acc(0u, 128u, (uint32_t)N);
       int it = 0;
       for (int lt = 0; lt < ntl; ++lt) {
-        const int ab = lt & 1;
-        const uint32_t aph = (uint32_t)(lt >> 1) & 1u;
+        const int ab = lt % kAcc;
+        const uint32_t aph = (uint32_t)(lt / kAcc) & 1u;
         if (!mbar_wait(&acce[ab], aph ^ 1u, err, kErrAccEmpty)) break;
         tc_fence_after();
         const uint32_t dt = tmem + (uint32_t)(ab * N);
@@ -161,17 +175,73 @@ __global__ void __launch_bounds__(192, 1)
       mma_commit(&drain);
       mbar_wait(&drain, 0u, err, kErrFull);
     }
+  } else if (warp >= 6) {
+    // --------------------------------------------------- dense columns (FP64)
+    const int dl = threadIdx.x - 192;  // 0..63
+    for (int64_t j = blockIdx.x; j <= X.c; j += gridDim.x) {
+      double dot[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) dot[b] = 0.0;
+      if (j >= 1) {
+        const double *cv = X.cov + (j - 1) * X.n;
+        for (int64_t i = dl; i < X.n; i += 64) {
+          const double x = __ldg(cv + i);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) dot[b] = fma(x, F.theta[i * NB + b], dot[b]);
+        }
+      }
+      // reduce over the 64 dense threads (two warps) through shared memory
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        for (int o = 16; o; o >>= 1) dot[b] += __shfl_xor_sync(0xffffffffu, dot[b], o);
+      }
+      __shared__ double s_dot[2][NB];
+      if (lane == 0)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) s_dot[warp - 6][b] = dot[b];
+      asm volatile("bar.sync 1, 64;" ::: "memory");
+      if (dl == 0) {
+        const double aj = X.a[j], bj = X.b[j];
+        const int g = block_of_tc(F.block_ptr, F.G, j);
+        const double eta = F.eta[g], ie = F.inv_eta[g];
+        bool act = false;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          if (sIdle[b]) continue;
+          const double s = aj * (s_dot[0][b] + s_dot[1][b]) + bj * sS[b];
+          const double lamj = F.lam[b] * F.omega[j];
+          const double bo = bcur[j * NB + b];
+          if (j >= 1) rbl[b] = fmax(rbl[b], dist_l1_tc(s, lamj, bo));
+          const double av = eta * bo + s;
+          const double bn = (fmax(av - lamj, 0.0) - fmax(-av - lamj, 0.0)) * ie;
+          bnxt[j * NB + b] = bn;
+          ctl[b] = fma(bj, bn, ctl[b]);
+          act = act || (bn != 0.0 && j >= 1);
+        }
+        if (act) s_dense_act[s_ndense++] = (int)j;
+      }
+      asm volatile("bar.sync 1, 64;" ::: "memory");
+    }
   } else {
     // -------------------------------------------------------------- epilogue
     const int q = warp & 3;           // TMEM lane quarter of this warp
     const int m = q * 32 + lane;      // tile row = column within the tile
-    const int et = m;                 // epilogue thread index 0..127
-    double rbl[NB], ctl[NB], wml[NB];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) { rbl[b] = 0.0; ctl[b] = 0.0; wml[b] = 0.0; }
+    const double dscale = ldexp(1.0, -4 * D);
     for (int lt = 0; lt < ntl; ++lt) {
-      const int ab = lt & 1;
-      const uint32_t aph = (uint32_t)(lt >> 1) & 1u;
+      const int ab = lt % kAcc;
+      const uint32_t aph = (uint32_t)(lt / kAcc) & 1u;
+      // operands of this thread's column, fetched while the MMAs run
+      const int tile = blockIdx.x + lt * gridDim.x;
+      const int64_t sidx = (int64_t)tile * 128 + m;
+      const bool live = sidx < X.p;
+      const int64_t j = 1 + X.c + (live ? sidx : 0);
+      const double aj = __ldg(X.a + j), bj = __ldg(X.b + j);
+      const double om = __ldg(F.omega + j);
+      double bo[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) bo[b] = bcur[j * NB + b];
+      const int g = block_of_tc(F.block_ptr, F.G, j);
+      const double eta = __ldg(F.eta + g), ie = __ldg(F.inv_eta + g);
       if (!mbar_wait(&accf[ab], aph, err, kErrAccFull)) break;
       tc_fence_after();
       uint32_t r[N];
@@ -181,14 +251,7 @@ __global__ void __launch_bounds__(192, 1)
       tmem_wait_ld();
       tc_fence_before();
       mbar_arrive(&acce[ab]);
-      const int tile = blockIdx.x + lt * gridDim.x;
-      const int64_t sidx = (int64_t)tile * 128 + m;
-      if (sidx >= X.p) continue;
-      const int64_t j = 1 + X.c + sidx;
-      const double aj = __ldg(X.a + j), bj = __ldg(X.b + j);
-      const double om = __ldg(F.omega + j);
-      const int g = block_of_tc(F.block_ptr, F.G, j);
-      const double eta = __ldg(F.eta + g), ie = __ldg(F.inv_eta + g);
+      if (!live) continue;
       bool act = false;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
@@ -199,13 +262,13 @@ __global__ void __launch_bounds__(192, 1)
           const float f = __uint_as_float(r[b * D + d]) * 512.0f;
           V = V * 16 + (long long)__float2int_rn(f);
         }
-        const double dot = (double)V * (sScale[b] * ldexp(1.0, -4 * D));
+        const double dot = (double)V * (sScale[b] * dscale);
         const double s = aj * dot + bj * sS[b];
         const double lamj = F.lam[b] * om;
-        const double bo = bcur[j * NB + b];
         if (!sIdle[b]) {
-          rbl[b] = fmax(rbl[b], dist_l1_tc(s, lamj, bo));
-          const double av = eta * bo + s;
+          rbl[b] = fmax(rbl[b], dist_l1_tc(s, lamj, bo[b]));
+          // eq. beta_update with M_g = eta_g I
+          const double av = eta * bo[b] + s;
           const double bn = (fmax(av - lamj, 0.0) - fmax(-av - lamj, 0.0)) * ie;
           bnxt[j * NB + b] = bn;
           ctl[b] = fma(bj, bn, ctl[b]);
@@ -215,12 +278,6 @@ __global__ void __launch_bounds__(192, 1)
       }
       if (act) flags[lt * 128 + m] = 1;
     }
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      red_rb[et][b] = rbl[b];
-      red_ct[et][b] = ctl[b];
-      red_wm[et][b] = wml[b];
-    }
   }
   __syncthreads();
   if (warp == 1) {
@@ -228,21 +285,23 @@ __global__ void __launch_bounds__(192, 1)
     tmem_dealloc(tmem, Sh::TMEM_COLS);
   }
   // per-CTA reductions in a fixed order
-  if (threadIdx.x < NB) {
-    const int b = threadIdx.x;
-    double mx = 0.0, c = 0.0, wm = 0.0;
-    for (int t = 0; t < 128; ++t) {
-      mx = fmax(mx, red_rb[t][b]);
-      c += red_ct[t][b];
-      wm = fmax(wm, red_wm[t][b]);
+  for (int b = 0; b < NB; ++b) {
+    red[0][threadIdx.x] = rbl[b];
+    red[1][threadIdx.x] = ctl[b];
+    red[2][threadIdx.x] = wml[b];
+    __syncthreads();
+    const int ops[3] = {0, 1, 0};
+    tree_reduce<3>(red, ops, 256);
+    if (threadIdx.x == 0) {
+      F.a_rb[blockIdx.x * NB + b] = red[0][0];
+      F.a_ct[blockIdx.x * NB + b] = red[1][0];
+      F.a_wmax[blockIdx.x * NB + b] = red[2][0];
     }
-    F.a_rb[blockIdx.x * NB + b] = mx;
-    F.a_ct[blockIdx.x * NB + b] = c;
-    F.a_wmax[blockIdx.x * NB + b] = wm;
+    __syncthreads();
   }
   // ordered compaction of the active flags (local tile order)
-  const int per = (T + Sh::THREADS - 1) / Sh::THREADS;
-  const int t0 = min(T, (int)threadIdx.x * per), t1 = min(T, t0 + per);
+  const int per = (TF + Sh::THREADS - 1) / Sh::THREADS;
+  const int t0 = min(TF, (int)threadIdx.x * per), t1 = min(TF, t0 + per);
   int cnt = 0;
   for (int t = t0; t < t1; ++t) cnt += flags[t];
   scan[threadIdx.x] = cnt;
@@ -260,96 +319,17 @@ __global__ void __launch_bounds__(192, 1)
       const int64_t tile = blockIdx.x + (int64_t)(t >> 7) * gridDim.x;
       lst[pos++] = (int)(1 + X.c + tile * 128 + (t & 127));
     }
-  if (threadIdx.x == Sh::THREADS - 1) F.a_cnt[blockIdx.x] = scan[Sh::THREADS - 1];
-}
-
-// Dense columns 0..c (intercept and covariates) of the tensor-core column
-// pass, in FP64, owning partial slot gridA - 1. One warp per column.
-template <int NB>
-__global__ void __launch_bounds__(256) k_col_dense(Dsg X, Fits F, int off, int slot) {
-  __shared__ double red_rb[8][NB], red_ct[8][NB];
-  __shared__ int sflag[64];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = *F.it_base + off;
-  const double *bcur = F.beta[k & 1];
-  double *bnxt = F.beta[(k & 1) ^ 1];
-  double S[NB];
-  bool idle[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const double *cp = F.c_part[k & 1];
-    double Ssum = 0.0;
-    for (int c = 0; c < F.gridC; ++c) Ssum += cp[(c * NB + b) * kCPartials + 2];
-    S[b] = Ssum;
-    idle[b] = (b >= F.nb) || (F.done[b] >= 0);
+  if (threadIdx.x == Sh::THREADS - 1) {
+    int tot = scan[Sh::THREADS - 1];
+    for (int d = 0; d < s_ndense; ++d) lst[tot++] = s_dense_act[d];
+    F.a_cnt[blockIdx.x] = tot;
   }
-  for (int t = threadIdx.x; t < 64; t += blockDim.x) sflag[t] = 0;
-  double rbl[NB], ctl[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) { rbl[b] = 0.0; ctl[b] = 0.0; }
-  __syncthreads();
-  for (int64_t j = warp; j <= X.c; j += 8) {
-    double dot[NB];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) dot[b] = 0.0;
-    if (j >= 1) {
-      const double *cv = X.cov + (j - 1) * X.n;
-      for (int64_t i = lane; i < X.n; i += 32) {
-        const double x = __ldg(cv + i);
-#pragma unroll
-        for (int b = 0; b < NB; ++b) dot[b] = fma(x, F.theta[i * NB + b], dot[b]);
-      }
-#pragma unroll
-      for (int b = 0; b < NB; ++b)
-        for (int o = 16; o; o >>= 1) dot[b] += __shfl_xor_sync(0xffffffffu, dot[b], o);
-    }
-    if (lane == 0) {
-      const double aj = X.a[j], bj = X.b[j];
-      const int g = block_of_tc(F.block_ptr, F.G, j);
-      const double eta = F.eta[g], ie = F.inv_eta[g];
-      bool act = false;
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        if (idle[b]) continue;
-        const double s = aj * dot[b] + bj * S[b];
-        const double lamj = F.lam[b] * F.omega[j];
-        const double bo = bcur[j * NB + b];
-        if (j >= 1) rbl[b] = fmax(rbl[b], dist_l1_tc(s, lamj, bo));
-        const double av = eta * bo + s;
-        const double bn = (fmax(av - lamj, 0.0) - fmax(-av - lamj, 0.0)) * ie;
-        bnxt[j * NB + b] = bn;
-        ctl[b] = fma(bj, bn, ctl[b]);
-        act = act || (bn != 0.0 && j >= 1);
-      }
-      if (act) sflag[j] = 1;
-    }
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int b = 0; b < NB; ++b) { red_rb[warp][b] = rbl[b]; red_ct[warp][b] = ctl[b]; }
-  __syncthreads();
-  if (threadIdx.x < NB) {
-    const int b = threadIdx.x;
-    double mx = 0.0, c = 0.0;
-    for (int w = 0; w < 8; ++w) { mx = fmax(mx, red_rb[w][b]); c += red_ct[w][b]; }
-    F.a_rb[slot * NB + b] = mx;
-    F.a_ct[slot * NB + b] = c;
-    F.a_wmax[slot * NB + b] = 0.0;
-  }
-  if (threadIdx.x == 0) {
-    int cnt = 0;
-    int *lst = F.a_list + (int64_t)slot * F.T;
-    for (int j = 1; j <= X.c; ++j)
-      if (sflag[j]) lst[cnt++] = j;
-    F.a_cnt[slot] = cnt;
-  }
+  col_finalize<NB>(F);
 }
 
 // theta^k_b / scale_b rounded to a 4D-bit fixed-point integer, written as D
 // balanced base-16 digits encoded as E4M3 bytes, row b*D + d of an N x npad
 // byte matrix (rows >= NB*D stay zero).
-__constant__ uint8_t kE4M3Int[17] = {0xD0, 0xCE, 0xCC, 0xCA, 0xC8, 0xC4, 0xC0, 0xB8, 0x00,
-                                     0x38, 0x40, 0x44, 0x48, 0x4A, 0x4C, 0x4E, 0x50};
 
 template <int NB, int D>
 __global__ void __launch_bounds__(256) k_quantize_tc(Fits F, int off, uint8_t *dg) {
@@ -357,9 +337,7 @@ __global__ void __launch_bounds__(256) k_quantize_tc(Fits F, int off, uint8_t *d
   __shared__ double sInv[kMaxNB];
   if (threadIdx.x < NB) {
     const int b = threadIdx.x;
-    const double *cp = F.c_part[k & 1];
-    double m = 0.0;
-    for (int c = 0; c < F.gridC; ++c) m = fmax(m, cp[(c * NB + b) * kCPartials + 3]);
+    const double m = F.tot_c[k & 1][b * kCPartials + 3];
     int E = 0;
     if (m > 0.0) frexp(m, &E);
     const double scale = (m > 0.0) ? ldexp(1.0, E + 1) : 1.0;
@@ -380,9 +358,301 @@ __global__ void __launch_bounds__(256) k_quantize_tc(Fits F, int off, uint8_t *d
     Xq = (Xq - t) >> 4;
   }
   dig[0] = (int)Xq;
+  // K-chunk kc = i / 128 holds N rows of 128 bytes; row r's 16-byte chunk c
+  // sits at chunk position c ^ (r % 8) (the 128-byte swizzle)
+  constexpr int N = TcShape<NB, D>::N;
+  const int64_t kc = i >> 7;
+  const int c = (int)((i & 127) >> 4), bt = (int)(i & 15);
 #pragma unroll
-  for (int d = 0; d < D; ++d) dg[(int64_t)(b * D + d) * F.npad + i] = kE4M3Int[dig[d] + 8];
+  for (int d = 0; d < D; ++d) {
+    const int r = b * D + d;
+    dg[kc * (N * 128) + r * 128 + ((c ^ (r & 7)) << 4) + bt] = kE4M3Int[dig[d] + 8];
+  }
 }
+
+// Copies the stored int8 columns into tiles of 128 columns x 128 samples,
+// each the byte image of a 128-byte-swizzled K-major operand: tile (t, kc)
+// at xt + (t*nk + kc)*16384, row m = column 128t + m, 16-byte chunk c of the
+// row at chunk position c ^ (m % 8); samples >= n and columns >= p are 0.
+__global__ void k_tile_x(Dsg X, uint8_t *xt, int64_t nk) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte chunk
+  const int64_t ntile = (X.p + 127) / 128;
+  if (g >= ntile * nk * 1024) return;
+  const int64_t tk = g >> 10;          // tile * nk + kc
+  const int w = (int)(g & 1023);       // chunk within the 16 KB tile
+  const int m = w >> 3, cp = w & 7;    // row, stored chunk position
+  const int c = cp ^ (m & 7);          // logical chunk
+  const int64_t t = tk / nk, kc = tk - t * nk;
+  const int64_t col = t * 128 + m;
+  const int64_t s0 = kc * 128 + c * 16;
+  uint4 v = make_uint4(0u, 0u, 0u, 0u);
+  if (col < X.p && s0 < X.n) {
+    const uint8_t *src = X.geno + col * X.ld + s0;
+    if (s0 + 16 <= X.n) {
+      v = *reinterpret_cast<const uint4 *>(src);
+    } else {
+      uint8_t b[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) b[q] = (s0 + q < X.n) ? src[q] : (uint8_t)0;
+      v = *reinterpret_cast<const uint4 *>(b);
+    }
+  }
+  *reinterpret_cast<uint4 *>(xt + tk * 16384 + (int64_t)w * 16) = v;
+}
+
+// ============================================================ X~ beta (TC)
+
+// Tensor-core X~ beta over the active stored columns (mixed path):
+// q_i = sum_{j active} x_ij w_j with w_jb = a_j beta_jb rounded to a
+// 4*DWD-bit fixed-point integer (scale 2^(E_b+1) > 2 max|w_b|) and split
+// into DWD balanced base-16 digits (E4M3).
+//   k_xprep      one thread per active position: its stored column and
+//                the digit bytes, written as the byte image of one K-major
+//                swizzled operand tile per block of 128 active positions;
+//   k_xbeta_tc   CTA (rt, sp): samples [128 rt, +128) (M, the TMEM lanes)
+//                over the blocks of split sp. One thread streams a ring of
+//                stages: TMA tile::gather4 brings the 128-byte sample runs of
+//                4 active columns at a time into an MN-major operand, a bulk
+//                copy brings the block's digit tile, and kind::f8f6f4 MMAs
+//                accumulate exact integer sums in FP32 in TMEM. The epilogue
+//                writes one exact int64 partial per (split, sample, fit).
+template <int NB, int DWD>
+struct XbShape {
+  static constexpr int NR = NB * DWD;
+  static constexpr int N = ((NR + 15) / 16) * 16;
+  static constexpr int A_BYTES = 128 * 128;
+  static constexpr int B_BYTES = N * 128;
+  static constexpr int BUF = A_BYTES + B_BYTES;
+  static constexpr int STAGES = 4;
+  static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+};
+
+constexpr int kXTMaxSplits = 16;
+
+template <int NB, int DWD>
+__global__ void __launch_bounds__(128)
+    k_xprep(Dsg X, Fits F, int off, const double *__restrict__ beta_in, int *__restrict__ scol,
+            uint8_t *__restrict__ wtile) {
+  using Sh = XbShape<NB, DWD>;
+  extern __shared__ int spre[];  // gridA + 1
+  __shared__ double sInv[kMaxNB];
+  const double *beta = beta_in;
+  if (beta == nullptr) {
+    const int k = *F.it_base + off;
+    beta = F.beta[(k & 1) ^ 1];
+  }
+  const int gA = F.gridA;
+  const int A = __ldcg(F.a_pre + gA);
+  const int nkb = (A + 127) / 128;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    F.meta_i[0] = max(1, min(kXTMaxSplits, nkb));
+    F.meta_i[1] = A;
+  }
+  if (threadIdx.x < NB) {
+    const int b = threadIdx.x;
+    const double m = F.tot_a[b * 3 + 2];
+    int E = 0;
+    if (m > 0.0) frexp(m, &E);
+    const double scale = (m > 0.0) ? ldexp(1.0, E + 1) : 1.0;
+    sInv[b] = ldexp(1.0, 4 * DWD) / scale;
+    if (blockIdx.x == 0) {
+      F.meta_d[b] = F.tot_a[b * 3 + 1];
+      F.meta_d[kMaxNB + b] = scale;
+    }
+  }
+  if (blockIdx.x >= nkb) return;
+  for (int t = threadIdx.x; t <= gA; t += 128) spre[t] = __ldcg(F.a_pre + t);
+  __syncthreads();
+  const int a = blockIdx.x * 128 + threadIdx.x;
+  int j = -1;
+  if (a < A) {
+    int lo = 0, hi = gA;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (spre[mid] <= a) lo = mid; else hi = mid;
+    }
+    j = F.a_list[(int64_t)lo * F.T + (a - spre[lo])];
+    if (j <= X.c) j = -1;  // covariates are summed in FP64 by k_vec
+  }
+  scol[a] = (j >= 0) ? (int)(j - 1 - X.c) : (int)X.p;
+  uint8_t *tile = wtile + (int64_t)blockIdx.x * Sh::B_BYTES;
+  const int t = threadIdx.x, ch = t >> 4, bt = t & 15;
+  const double aj = (j >= 0) ? __ldg(X.a + j) : 0.0;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    long long W = (j >= 0) ? __double2ll_rn(aj * beta[(int64_t)j * NB + b] * sInv[b]) : 0;
+    int dig[DWD];
+#pragma unroll
+    for (int d = DWD - 1; d >= 1; --d) {
+      const int tt = (int)(((W + 8) & 15) - 8);
+      dig[d] = tt;
+      W = (W - tt) >> 4;
+    }
+    dig[0] = (int)W;
+#pragma unroll
+    for (int d = 0; d < DWD; ++d) {
+      const int r = b * DWD + d;
+      tile[r * 128 + ((ch ^ (r & 7)) << 4) + bt] = kE4M3Int[dig[d] + 8];
+    }
+  }
+  // digit rows beyond NB*DWD are zero
+  for (int r = NB * DWD; r < Sh::N; ++r) tile[r * 128 + ((ch ^ (r & 7)) << 4) + bt] = 0;
+}
+
+template <int NB, int DWD>
+__global__ void __launch_bounds__(128)
+    k_xbeta_tc(Dsg X, Fits F, const int *__restrict__ scol, const uint8_t *__restrict__ wtile,
+               const __grid_constant__ CUtensorMap tmX, int *err) {
+  using Sh = XbShape<NB, DWD>;
+  constexpr int N = Sh::N;
+  constexpr int ST = Sh::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[ST], empty[ST], dbar;
+  __shared__ uint32_t tmem_base;
+  const uint32_t base_u32 = smem_u32(smem_raw);
+  uint8_t *ring = smem_raw + (((base_u32 + 1023u) & ~1023u) - base_u32);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int A = F.meta_i[1];
+  const int nkb = (A + 127) / 128;
+  const int S = F.meta_i[0];
+  if ((int)blockIdx.y >= S) return;
+  const int kb0 = (int)((int64_t)nkb * blockIdx.y / S), kb1 = (int)((int64_t)nkb * (blockIdx.y + 1) / S);
+  const int64_t i0 = (int64_t)blockIdx.x * 128;
+  long long *out = F.xb_ipart + (int64_t)blockIdx.y * F.npad * NB;
+  if (kb1 <= kb0) {
+    const int64_t i = i0 + tid;
+    if (i < F.npad)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) out[i * NB + b] = 0;
+    return;
+  }
+  if (tid == 0) {
+    for (int q = 0; q < ST; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
+    mbar_init(&dbar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, Sh::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  if (warp == 0) {
+    // warp 0 streams the blocks: lane l gathers active columns 4l..4l+3 of
+    // a block; lane 0 also loads the digit tile and issues the MMAs
+    const int lane = tid & 31;
+    const uint32_t idesc = idesc_f32acc_amn(0u, 128u, (uint32_t)N);
+    const int nb = kb1 - kb0;
+    bool ok = true;
+    for (int it = 0; it < nb + ST; ++it) {
+      if (it < nb) {
+        const int s = it % ST;
+        const uint32_t ph = (uint32_t)(it / ST) & 1u;
+        int okl = 1;
+        if (lane == 0) {
+          okl = mbar_wait(&empty[s], ph ^ 1u, err, kErrEmpty) ? 1 : 0;
+          if (okl) {
+            mbar_arrive_expect_tx(&full[s], Sh::BUF);
+            bulk_load(ring + s * Sh::BUF + Sh::A_BYTES, wtile + (int64_t)(kb0 + it) * Sh::B_BYTES, Sh::B_BYTES,
+                      &full[s]);
+          }
+        }
+        okl = __shfl_sync(0xffffffffu, okl, 0);
+        if (!okl) { ok = false; break; }
+        const int4 c4 = __ldg(reinterpret_cast<const int4 *>(scol + (int64_t)(kb0 + it) * 128) + lane);
+        tma_gather4(ring + s * Sh::BUF + lane * 512, &tmX, &full[s], (int)i0, c4.x, c4.y, c4.z, c4.w);
+      }
+      const int mt = it - (ST - 1);
+      if (lane == 0 && mt >= 0 && mt < nb) {
+        const int s = mt % ST;
+        const uint32_t ph = (uint32_t)(mt / ST) & 1u;
+        if (!mbar_wait(&full[s], ph, err, kErrFull)) {
+          ok = false;
+        } else {
+          tc_fence_after();
+          const uint32_t sa = smem_u32(ring + s * Sh::BUF);
+          const uint64_t ad = sdesc_mn128(sa), bd = sdesc_k128(sa + Sh::A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma_f8(tmem, ad + (uint64_t)(kk * 256), bd + (uint64_t)(kk * 2), idesc, (mt | kk) != 0 ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+      }
+      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+    }
+    if (lane == 0) mma_commit(&dbar);
+  }
+  __syncwarp();
+  const bool done = mbar_wait(&dbar, 0u, err, kErrAccFull);
+  tc_fence_after();
+  // epilogue: TMEM lane = sample row, columns b*DWD + d
+  {
+    uint32_t r[N];
+#pragma unroll
+    for (int c = 0; c < N / 16; ++c) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * c), r + 16 * c);
+    tmem_wait_ld();
+    const int64_t i = i0 + tid;
+    if (i < F.npad && done)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        long long V = 0;
+#pragma unroll
+        for (int d = 0; d < DWD; ++d) {
+          const float f = __uint_as_float(r[b * DWD + d]) * 512.0f;
+          V = V * 16 + (long long)__float2int_rn(f);
+        }
+        out[i * NB + b] = V;
+      }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, Sh::TMEM_COLS);
+  }
+}
+
+template <int NB, int DWD>
+size_t g_xt_opted = 48 * 1024;
+
+size_t xbeta_tc_smem(int NB, int DWD) {
+  const int N = ((NB * DWD + 15) / 16) * 16;
+  return (size_t)4 * (128 * 128 + N * 128) + 1024 + 16;
+}
+
+template <int NB, int DWD>
+static cudaError_t xbeta_tc_t(const Dsg &X, const Fits &F, int off, const double *beta_in,
+                              const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err,
+                              cudaStream_t s) {
+  const size_t smem = xbeta_tc_smem(NB, DWD);
+  if (smem > g_xt_opted<NB, DWD>) {
+    cudaError_t e = cudaFuncSetAttribute(k_xbeta_tc<NB, DWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    g_xt_opted<NB, DWD> = smem;
+  }
+  // the prep grid covers every possible block of 128 active positions
+  const int maxkb = (int)((X.P + 127) / 128);
+  const size_t psmem = (size_t)(F.gridA + 1) * sizeof(int);
+  k_xprep<NB, DWD><<<maxkb, 128, psmem, s>>>(X, F, off, beta_in, scol, wtile);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((X.n + 127) / 128), kXTMaxSplits);
+  k_xbeta_tc<NB, DWD><<<grid, 128, smem, s>>>(X, F, scol, wtile, tmX, err);
+  return cudaGetLastError();
+}
+
+// scol: (P + 127)/128*128 ints; wtile: (P + 127)/128 tiles of N*128 bytes.
+cudaError_t launch_xbeta_tc(int NB, const Dsg &X, const Fits &F, int off, const double *beta_in,
+                            const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err, cudaStream_t s) {
+  switch (NB) {
+    case 1: return xbeta_tc_t<1, 11>(X, F, off, beta_in, tmX, scol, wtile, err, s);
+    case 2: return xbeta_tc_t<2, 11>(X, F, off, beta_in, tmX, scol, wtile, err, s);
+    case 3: return xbeta_tc_t<3, 11>(X, F, off, beta_in, tmX, scol, wtile, err, s);
+    case 4: return xbeta_tc_t<4, 11>(X, F, off, beta_in, tmX, scol, wtile, err, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int xbeta_tc_rows(int NB) { return ((NB * 11 + 15) / 16) * 16; }
 
 // ------------------------------------------------------------------ host
 
@@ -391,12 +661,12 @@ size_t g_tc_opted = 48 * 1024;
 
 size_t col_tc_smem(int NB, int D, int T) {
   int N = NB * D <= 16 ? 16 : (NB * D <= 32 ? 32 : 64);
-  return (size_t)6 * (128 * 128 + N * 128) + 1024 + (size_t)T + 16;
+  return (size_t)6 * (128 * 128 + N * 128) + 1024 + (size_t)T + 16;  // flags use <= T bytes
 }
 
 template <int NB, int D>
-static cudaError_t col_tc_t(const Dsg &X, const Fits &F, int off, const CUtensorMap &tmX,
-                            const CUtensorMap &tmD, int grid, int tiles_per_cta, int *err,
+static cudaError_t col_tc_t(const Dsg &X, const Fits &F, int off, const uint8_t *xt,
+                            const uint8_t *dgt, int grid, int tiles_per_cta, int *err,
                             cudaStream_t s) {
   const size_t smem = col_tc_smem(NB, D, F.T);
   if (smem > g_tc_opted<NB, D>) {
@@ -404,30 +674,19 @@ static cudaError_t col_tc_t(const Dsg &X, const Fits &F, int off, const CUtensor
     if (e != cudaSuccess) return e;
     g_tc_opted<NB, D> = smem;
   }
-  k_col_tc<NB, D><<<grid, TcShape<NB, D>::THREADS, smem, s>>>(X, F, off, tmX, tmD, tiles_per_cta, err);
+  k_col_tc<NB, D><<<grid, TcShape<NB, D>::THREADS, smem, s>>>(X, F, off, xt, dgt, tiles_per_cta, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, const CUtensorMap &tmX,
-                          const CUtensorMap &tmD, int grid, int tiles_per_cta, int *err,
+cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, const uint8_t *xt,
+                          const uint8_t *dgt, int grid, int tiles_per_cta, int *err,
                           cudaStream_t s) {
 #define FSQR_TC_CASE(nb, d) \
-  if (NB == nb && D == d) return col_tc_t<nb, d>(X, F, off, tmX, tmD, grid, tiles_per_cta, err, s);
+  if (NB == nb && D == d) return col_tc_t<nb, d>(X, F, off, xt, dgt, grid, tiles_per_cta, err, s);
   FSQR_TC_CASE(1, 7) FSQR_TC_CASE(2, 7) FSQR_TC_CASE(3, 7) FSQR_TC_CASE(4, 7)
   FSQR_TC_CASE(1, 6) FSQR_TC_CASE(2, 6) FSQR_TC_CASE(3, 6) FSQR_TC_CASE(4, 6)
 #undef FSQR_TC_CASE
   return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_col_dense(int NB, const Dsg &X, const Fits &F, int off, int slot, cudaStream_t s) {
-  switch (NB) {
-    case 1: k_col_dense<1><<<1, 256, 0, s>>>(X, F, off, slot); break;
-    case 2: k_col_dense<2><<<1, 256, 0, s>>>(X, F, off, slot); break;
-    case 3: k_col_dense<3><<<1, 256, 0, s>>>(X, F, off, slot); break;
-    case 4: k_col_dense<4><<<1, 256, 0, s>>>(X, F, off, slot); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_quantize_tc(int NB, int D, const Fits &F, int off, uint8_t *dg, cudaStream_t s) {
@@ -442,5 +701,12 @@ cudaError_t launch_quantize_tc(int NB, int D, const Fits &F, int off, uint8_t *d
 }
 
 int tc_rows(int NB, int D) { return NB * D <= 16 ? 16 : (NB * D <= 32 ? 32 : 64); }
+
+cudaError_t launch_tile_x(const Dsg &X, uint8_t *xt, int64_t nk, cudaStream_t s) {
+  const int64_t chunks = (X.p + 127) / 128 * nk * 1024;
+  if (chunks == 0) return cudaSuccess;
+  k_tile_x<<<(unsigned)((chunks + 255) / 256), 256, 0, s>>>(X, xt, nk);
+  return cudaGetLastError();
+}
 
 }  // namespace fsqr

@@ -75,6 +75,14 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -168,6 +176,42 @@ __device__ __forceinline__ bool elect_one() {
       "selp.b32 %0, 1, 0, P;\n}\n"
       : "=r"(pred));
   return pred != 0;
+}
+
+}  // namespace sm103
+}  // namespace fsqr
+
+namespace fsqr {
+namespace sm103 {
+
+// TMA gather of 4 rows (y0..y3) of a 2-D tensor, each box0 elements wide from
+// column x, into 4 consecutive box rows in shared memory (box one row high).
+__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y0,
+                                            int y1, int y2, int y3) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5, %6}], [%7];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3),
+        "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory descriptor of an MN-major operand with the 128-byte swizzle:
+// 128-byte rows hold 128 consecutive M elements (8-bit) of one k; 8 rows form
+// a 1024-byte atom and atoms follow each other along K every 1024 bytes.
+__device__ __forceinline__ uint64_t sdesc_mn128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(1024u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// As idesc_f32acc with the A operand MN-major (bit 15).
+__device__ __forceinline__ uint32_t idesc_f32acc_amn(uint32_t ab_fmt, uint32_t M, uint32_t N) {
+  return idesc_f32acc(ab_fmt, M, N) | (1u << 15);
 }
 
 }  // namespace sm103
