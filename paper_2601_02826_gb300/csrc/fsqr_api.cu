@@ -55,6 +55,13 @@ int fail(fsqr_ctx *ctx, int code, const char *fmt, ...) {
                   __FILE__, __LINE__);                                                    \
   } while (0)
 
+// A kernel launch through a launcher: counted, then checked.
+#define LK(call)                       \
+  do {                                 \
+    ctx->pf.kernel_launches += 1;      \
+    CK(call);                          \
+  } while (0)
+
 #define TRY(expr)              \
   do {                         \
     int rc_ = (expr);          \
@@ -219,10 +226,10 @@ int prepare(fsqr_ctx *ctx, const fsqr_design *d, Prep *pp, bool need_colbound) {
   TRY(wsget(ctx, "aff_b", X.P, &b));
   TRY(wsget(ctx, "stat_missing", 1, &miss));
   CK(cudaMemsetAsync(miss, 0, sizeof(int), ctx->stream));
-  CK(launch_col_stats(X, mean, sd, miss, ctx->stream));
+  LK(launch_col_stats(X, mean, sd, miss, ctx->stream));
   p.mean = d->col_mean ? d->col_mean : mean;
   p.sd = d->col_sd ? d->col_sd : sd;
-  CK(launch_affine(X, p.mean, p.sd, d->standardize, a, b, ctx->stream));
+  LK(launch_affine(X, p.mean, p.sd, d->standardize, a, b, ctx->stream));
   X.a = a;
   X.b = b;
   int hmiss = 0;
@@ -230,7 +237,7 @@ int prepare(fsqr_ctx *ctx, const fsqr_design *d, Prep *pp, bool need_colbound) {
   if (need_colbound) {
     double *cb;
     TRY(wsget(ctx, "colbound", 1, &cb));
-    CK(launch_colbound(X, p.mean, cb, ctx->stream));
+    LK(launch_colbound(X, p.mean, cb, ctx->stream));
     CK(cudaMemcpyAsync(&p.colbound, cb, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   }
   CK(cudaStreamSynchronize(ctx->stream));
@@ -279,7 +286,7 @@ int nb_template(int nb) {
 int y_stats(fsqr_ctx *ctx, const double *y, int64_t n, double *ymax, double *ysd) {
   double *st;
   TRY(wsget(ctx, "ystats", 3, &st));
-  CK(launch_vec_stats(y, n, st, ctx->stream));
+  LK(launch_vec_stats(y, n, st, ctx->stream));
   double h[3];
   CK(cudaMemcpyAsync(h, st, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -315,12 +322,12 @@ int lambda_max_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, 
   int64_t k = (int64_t)ceil((double)n * tau);
   if (k < 1) k = 1;
   if (k > n) k = n;
-  CK(launch_select(y, n, k, q, ctx->stream));
-  CK(launch_lmax_vec(y, n, npad, tau, q, v, ctx->stream));
-  CK(launch_sum_cols(v, n, npad, 1, vs, nullptr, ctx->stream));
+  LK(launch_select(y, n, k, q, ctx->stream));
+  LK(launch_lmax_vec(y, n, npad, tau, q, v, ctx->stream));
+  LK(launch_sum_cols(v, n, npad, 1, vs, nullptr, ctx->stream));
   Fits F = pass_fits(ctx, X);
-  CK(launch_col_pass(A_XT, 1, X, F, 0, v, vs, s, nullptr, ctx->stream));
-  CK(launch_colmax_ratio(s, omega, X.P, (double)n, o, ctx->stream));
+  LK(launch_col_pass(A_XT, 1, X, F, 0, v, vs, s, nullptr, ctx->stream));
+  LK(launch_colmax_ratio(s, omega, X.P, (double)n, o, ctx->stream));
   CK(cudaMemcpyAsync(out, o, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return FSQR_OK;
@@ -360,7 +367,7 @@ int eta_impl(fsqr_ctx *ctx, const Prep &pr, const int64_t *bp, int G, double mu,
   CK(cudaMemcpyAsync(d_splits, splits.data(), splits.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(d_sob, sob.data(), sob.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(d_bp, bp, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
-  CK(launch_power_init(v, d_bp, G, P, ctx->stream));
+  LK(launch_power_init(v, d_bp, G, P, ctx->stream));
   Fits F = pass_fits(ctx, X);
   F.block_ptr = d_bp;
   F.G = G;
@@ -368,10 +375,10 @@ int eta_impl(fsqr_ctx *ctx, const Prep &pr, const int64_t *bp, int G, double mu,
   std::vector<char> frozen(G, 0);
   int left = G;
   for (int t = 1; t <= max_iter && left > 0; ++t) {
-    CK(launch_xv_blocks(X, v, d_splits, d_sob, G, nsplit, U, npad, part, ctx->stream));
-    CK(launch_sum_cols(U, n, npad, G, usum, usq, ctx->stream));
-    CK(launch_col_pass(A_XT_BLOCK, 1, X, F, 0, U, usum, w, nullptr, ctx->stream));
-    CK(launch_power_step(w, d_bp, G, P, v, wn, ctx->stream));
+    LK(launch_xv_blocks(X, v, d_splits, d_sob, G, nsplit, U, npad, part, ctx->stream));
+    LK(launch_sum_cols(U, n, npad, G, usum, usq, ctx->stream));
+    LK(launch_col_pass(A_XT_BLOCK, 1, X, F, 0, U, usum, w, nullptr, ctx->stream));
+    LK(launch_power_step(w, d_bp, G, P, v, wn, ctx->stream));
     CK(cudaMemcpyAsync(hq.data(), usq, G * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(hw.data(), wn, G * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -535,7 +542,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     TRY(wsget(ctx, "g_err", 1, &d_err));
     CK(cudaMemsetAsync(dg, 0, (size_t)(nk * N * 128), st));
     CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-    CK(launch_tile_x(X, xt, nk, st));
+    LK(launch_tile_x(X, xt, nk, st));
     // rows of the stored matrix (one column each) for the gathered X~ beta
     TRY(make_tmap_u8(ctx, &tmG, X.geno, (uint64_t)n, (uint64_t)X.p, (uint64_t)X.ld, 128, 1));
     const int64_t maxkb = (P + 127) / 128;
@@ -566,24 +573,24 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   CK(cudaMemsetAsync(F.beta[1], 0, sizeof(double) * P * NB, st));
   bool cold = true;
   for (int b = 0; b < nb; ++b) cold = cold && gs.src_fit[b] < 0;
-  CK(launch_init_state(NB, F, nb, cold ? FSQR_WARM_NONE : FSQR_WARM_GIVEN, st));
+  LK(launch_init_state(NB, F, nb, cold ? FSQR_WARM_NONE : FSQR_WARM_GIVEN, st));
   if (!cold) {
     // per slot: warm slots copy from the user's arrays, cold ones take y
     for (int b = 0; b < nb; ++b) {
       const int sf = gs.src_fit[b];
       if (sf >= 0) {
-        CK(launch_pack(E.beta + (int64_t)sf * P, P, F.beta[0] + b, P, 1, NB, P, st));
-        CK(launch_pack(E.z + (int64_t)sf * n, n, F.z + b, n, 1, NB, npad, st));
-        CK(launch_pack(E.theta + (int64_t)sf * n, n, F.theta + b, n, 1, NB, npad, st));
+        LK(launch_pack(E.beta + (int64_t)sf * P, P, F.beta[0] + b, P, 1, NB, P, st));
+        LK(launch_pack(E.z + (int64_t)sf * n, n, F.z + b, n, 1, NB, npad, st));
+        LK(launch_pack(E.theta + (int64_t)sf * n, n, F.theta + b, n, 1, NB, npad, st));
       } else {
-        CK(launch_pack(E.y, n, F.z + b, n, 1, NB, npad, st));
+        LK(launch_pack(E.y, n, F.z + b, n, 1, NB, npad, st));
       }
     }
   }
-  CK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, F.beta[0], st));
-  if (tc) CK(launch_xbeta_tc(NB, X, F, 0, F.beta[0], tmG, scol, wtile, d_err, st));
-  else CK(launch_xbeta(NB, X, F, 0, F.beta[0], st));
-  CK(launch_vec(NB, X, F, 0, 1, st));
+  LK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, F.beta[0], st));
+  if (tc) LK(launch_xbeta_tc(NB, X, F, 0, F.beta[0], tmG, scol, wtile, d_err, st));
+  else LK(launch_xbeta(NB, X, F, 0, F.beta[0], st));
+  LK(launch_vec(NB, X, F, 0, 1, st));
 
   // ---- the iteration as a captured graph of M steps
   const int K = F.K;
@@ -711,9 +718,9 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   for (int b = 0; b < nb; ++b) {
     const int k_fin = (hd[b] >= 0) ? hd[b] : host_base;
     const int f = gs.fit[b];
-    CK(launch_unpack(F.beta[k_fin & 1] + b, E.beta + (int64_t)f * P, P, P, 1, NB, st));
-    CK(launch_unpack(F.z + b, E.z + (int64_t)f * n, n, n, 1, NB, st));
-    CK(launch_unpack(F.theta + b, E.theta + (int64_t)f * n, n, n, 1, NB, st));
+    LK(launch_unpack(F.beta[k_fin & 1] + b, E.beta + (int64_t)f * P, P, P, 1, NB, st));
+    LK(launch_unpack(F.z + b, E.z + (int64_t)f * n, n, n, 1, NB, st));
+    LK(launch_unpack(F.theta + b, E.theta + (int64_t)f * n, n, n, 1, NB, st));
   }
   const double t_solve = now_ms() - t0;
 
@@ -729,18 +736,18 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     TRY(wsget(ctx, "r_lams", kMaxNB, &dlams));
     CK(cudaMemsetAsync(bfin, 0, sizeof(double) * P * NB, st));
     for (int b = 0; b < nb; ++b)
-      CK(launch_pack(E.beta + (int64_t)gs.fit[b] * P, P, bfin + b, P, 1, NB, P, st));
+      LK(launch_pack(E.beta + (int64_t)gs.fit[b] * P, P, bfin + b, P, 1, NB, P, st));
     CK(cudaMemcpyAsync(dtaus, F.tau, sizeof(double) * kMaxNB, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(dlams, F.lam, sizeof(double) * kMaxNB, cudaMemcpyHostToDevice, st));
     const double *schk_use = nullptr, *tc_use = nullptr;
     if (E.gap_defined) {
-      CK(launch_dual_point(NB, F.theta, n, npad, dtaus, nb, tc, tcs, st));
+      LK(launch_dual_point(NB, F.theta, n, npad, dtaus, nb, tc, tcs, st));
       Fits Fx = F;
-      CK(launch_col_pass(A_XT, NB, X, Fx, 0, tc, tcs, schk, nullptr, st));
+      LK(launch_col_pass(A_XT, NB, X, Fx, 0, tc, tcs, schk, nullptr, st));
       schk_use = schk;
       tc_use = tc;
     }
-    CK(launch_summary(NB, nb, n, P, E.y, F.z, F.r, bfin, E.omega, dtaus, dlams, schk_use, tc_use,
+    LK(launch_summary(NB, nb, n, P, E.y, F.z, F.r, bfin, E.omega, dtaus, dlams, schk_use, tc_use,
                       summ, st));
     double hs[kMaxNB * 8];
     CK(cudaMemcpyAsync(hs, summ, sizeof(double) * kMaxNB * 8, cudaMemcpyDeviceToHost, st));
@@ -802,7 +809,7 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
     double *d;
     TRY(wsget(ctx, "omega_chk", 2, &d));
     CK(cudaMemcpyAsync(d, omega, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(launch_min_omega(omega, P, d + 1, ctx->stream));
+    LK(launch_min_omega(omega, P, d + 1, ctx->stream));
     CK(cudaMemcpyAsync(om, d, sizeof om, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
   }
@@ -1131,17 +1138,17 @@ int fsqr_kkt(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, double tau, 
   TRY(wsget(ctx, "k_lam", 1, &dl));
   TRY(wsget(ctx, "k_om", 2, &om));
   // X~ beta
-  CK(launch_col_pass(A_LIST, 1, X, F, 0, nullptr, nullptr, nullptr, beta, st));
-  CK(launch_xbeta(1, X, F, 0, beta, st));
-  CK(launch_gather_xb(1, F, xb, npad, 1, st));
+  LK(launch_col_pass(A_LIST, 1, X, F, 0, nullptr, nullptr, nullptr, beta, st));
+  LK(launch_xbeta(1, X, F, 0, beta, st));
+  LK(launch_gather_xb(1, F, xb, npad, 1, st));
   // s = X~^T theta (padded copy of theta)
-  CK(launch_pack(theta, n, th, n, 1, 1, npad, st));
-  CK(launch_sum_cols(th, n, npad, 1, ths, nullptr, st));
-  CK(launch_col_pass(A_XT, 1, X, F, 0, th, ths, s, nullptr, st));
-  CK(launch_kkt_given(n, P, y, xb, z, theta, s, beta, omega, tau, lambda, o4, st));
+  LK(launch_pack(theta, n, th, n, 1, 1, npad, st));
+  LK(launch_sum_cols(th, n, npad, 1, ths, nullptr, st));
+  LK(launch_col_pass(A_XT, 1, X, F, 0, th, ths, s, nullptr, st));
+  LK(launch_kkt_given(n, P, y, xb, z, theta, s, beta, omega, tau, lambda, o4, st));
   CK(cudaMemcpyAsync(dt, &tau, sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(dl, &lambda, sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(launch_min_omega(omega, P, om, st));
+  LK(launch_min_omega(omega, P, om, st));
   double hom = 0.0, h4[4];
   CK(cudaMemcpyAsync(&hom, om, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h4, o4, sizeof h4, cudaMemcpyDeviceToHost, st));
@@ -1150,16 +1157,16 @@ int fsqr_kkt(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, double tau, 
   // X~ beta for r gives the primal loss of beta
   double *ypad;
   TRY(wsget(ctx, "k_ypad", (size_t)npad, &ypad));
-  CK(launch_pack(y, n, ypad, n, 1, 1, npad, st));
+  LK(launch_pack(y, n, ypad, n, 1, 1, npad, st));
   const bool gap_def = (P == 1) || (hom > 0.0);
   const double *schk_use = nullptr, *tc_use = nullptr;
   if (gap_def) {
-    CK(launch_dual_point(1, th, n, npad, dt, 1, tc, tcs, st));
-    CK(launch_col_pass(A_XT, 1, X, F, 0, tc, tcs, schk, nullptr, st));
+    LK(launch_dual_point(1, th, n, npad, dt, 1, tc, tcs, st));
+    LK(launch_col_pass(A_XT, 1, X, F, 0, tc, tcs, schk, nullptr, st));
     schk_use = schk;
     tc_use = tc;
   }
-  CK(launch_summary(1, 1, n, P, y, ypad, xb, beta, omega, dt, dl, schk_use, tc_use, summ, st));
+  LK(launch_summary(1, 1, n, P, y, ypad, xb, beta, omega, dt, dl, schk_use, tc_use, summ, st));
   double hs[8];
   CK(cudaMemcpyAsync(hs, summ, sizeof hs, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1214,10 +1221,10 @@ int fsqr_predict(fsqr_ctx *ctx, const fsqr_design *Xd, const double *beta, int B
     const int nb = std::min(kMaxNB, B - b0);
     const int NB = nb_template(nb);
     F.nb = nb;
-    CK(launch_pack(beta + (int64_t)b0 * P, P, bg, P, nb, NB, P, st));
-    CK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, bg, st));
-    CK(launch_xbeta(NB, X, F, 0, bg, st));
-    CK(launch_gather_xb(NB, F, out + (int64_t)b0 * n, n, nb, st));
+    LK(launch_pack(beta + (int64_t)b0 * P, P, bg, P, nb, NB, P, st));
+    LK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, bg, st));
+    LK(launch_xbeta(NB, X, F, 0, bg, st));
+    LK(launch_gather_xb(NB, F, out + (int64_t)b0 * n, n, nb, st));
   }
   CK(cudaStreamSynchronize(st));
   return FSQR_OK;
@@ -1248,7 +1255,7 @@ int fsqr_back_transform(fsqr_ctx *ctx, const fsqr_design *Xd, const double *beta
   if (!beta_std || !beta_out || B < 0) return fail(ctx, FSQR_EINVAL, "bad arguments");
   Prep pr;
   TRY(prepare(ctx, Xd, &pr, false));
-  CK(launch_back_transform(pr.X, beta_std, B, beta_out, ctx->stream));
+  LK(launch_back_transform(pr.X, beta_std, B, beta_out, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return FSQR_OK;
 }
