@@ -241,6 +241,34 @@ int fsqr_profile_enable(fsqr_ctx *ctx, int on);
 int fsqr_profile_get(fsqr_ctx *ctx, fsqr_profile *out);
 int fsqr_profile_reset(fsqr_ctx *ctx);
 
+/* ---- lambda_max without device allocation -------------------------------
+ * The paper has no counterpart: this entry point is a property of the
+ * library, not of the method. It computes exactly what fsqr_lambda_max
+ * computes, with the same kernels in the same order, but allocates no device
+ * memory. It is for callers that cannot allocate at call time: a serving
+ * process whose device memory is reserved up front by its own pool
+ * allocator, or one that cannot accept the device-wide synchronisation that
+ * cudaMalloc and cudaFree imply.
+ *
+ * Scratch: one static device array of FSQR_NOALLOC_SCRATCH_BYTES (8 MiB) per
+ * device, part of the library image. A call needs about 40*P + 8*pad16(n)
+ * bytes of it (P = 1 + c + p; each buffer rounded up to 256 bytes). Larger
+ * designs return FSQR_EINVAL, with the byte counts in fsqr_last_error; use
+ * fsqr_lambda_max for them. For example, n = 5,000 with P = 100,006 fits.
+ * Arguments, result, and the other errors are those of fsqr_lambda_max. The
+ * call is synchronous on the context's stream.
+ *
+ * The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress, once per device, with that device current) and may
+ * load kernel code. Make that first call before any stream capture begins.
+ * Every context on a device shares the array, and it keeps the previous
+ * call's contents. Calls that overlap in time on one device race: from
+ * several host threads, or from several contexts or streams. They then
+ * return wrong results. Serialise such calls. */
+#define FSQR_NOALLOC_SCRATCH_BYTES 8388608
+int fsqr_lambda_max_noalloc(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau,
+                            const double *omega, double *out);
+
 #ifdef __cplusplus
 }
 #endif

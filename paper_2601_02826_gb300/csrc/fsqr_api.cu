@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <chrono>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1257,6 +1258,143 @@ int fsqr_back_transform(fsqr_ctx *ctx, const fsqr_design *Xd, const double *beta
   TRY(prepare(ctx, Xd, &pr, false));
   LK(launch_back_transform(pr.X, beta_std, B, beta_out, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return FSQR_OK;
+}
+
+}  // extern "C"
+
+// ---- lambda_max without device allocation ----------------------------------
+//
+// fsqr_lambda_max takes its buffers from the context's workspace, which grows
+// by cudaMalloc on first use. Some callers cannot allocate at call time: a
+// serving process whose device memory is reserved up front by its own pool
+// (a caching allocator holding all free HBM), or one that cannot accept the
+// device-wide synchronisation that cudaMalloc/cudaFree imply. For them the
+// variant below runs the same kernels in the same order on buffers carved
+// from one static device array that is part of the library image.
+
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[FSQR_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Address of this device's copy of the array, looked up once per device with
+// that device current (the caller has selected it).
+int noalloc_base(fsqr_ctx *ctx, unsigned char **out) {
+  if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+    return fail(ctx, FSQR_EINVAL, "device %d >= %d", ctx->device, kNoAllocMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[ctx->device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return fail(ctx, FSQR_ECUDA, "cudaGetSymbolAddress of the static scratch: %s",
+                  cudaGetErrorString(e));
+    }
+    g_noalloc_addr[ctx->device] = p;
+  }
+  *out = static_cast<unsigned char *>(g_noalloc_addr[ctx->device]);
+  return FSQR_OK;
+}
+
+// Bump carving in 256-byte steps; with base == nullptr it only counts bytes.
+struct Carve {
+  unsigned char *base;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t count) {
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += (std::max<size_t>(count * sizeof(T), 1) + 255) / 256 * 256;
+    return p;
+  }
+};
+
+struct NoAllocBufs {
+  double *mean, *sd, *a, *b, *q, *v, *vs, *s, *o;
+  int *miss;
+};
+
+size_t noalloc_layout(unsigned char *base, int64_t n, int64_t P, NoAllocBufs *B) {
+  Carve c{base};
+  const size_t F = (size_t)(P - 1), npad = (size_t)pad16(n);
+  B->mean = c.take<double>(F);
+  B->sd = c.take<double>(F);
+  B->a = c.take<double>((size_t)P);
+  B->b = c.take<double>((size_t)P);
+  B->s = c.take<double>((size_t)P);
+  B->v = c.take<double>(npad);
+  B->q = c.take<double>(1);
+  B->vs = c.take<double>(1);
+  B->o = c.take<double>(1);
+  B->miss = c.take<int>(1);
+  return c.off;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fsqr_lambda_max_noalloc(fsqr_ctx *ctx, const fsqr_design *d, const double *y, double tau,
+                            const double *omega, double *out) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!y || !omega || !out) return fail(ctx, FSQR_EINVAL, "NULL argument");
+  if (!(tau > 0.0 && tau < 1.0)) return fail(ctx, FSQR_EINVAL, "tau must be in (0,1)");
+  TRY(check_design(ctx, d));
+  Dsg X{};
+  X.n = d->n;
+  X.p = d->p;
+  X.c = d->c;
+  X.P = 1 + d->c + d->p;
+  X.fmt = d->geno_format;
+  X.geno = static_cast<const uint8_t *>(d->geno);
+  X.ld = d->geno_ld;
+  X.cov = d->cov;
+  NoAllocBufs B;
+  const size_t need = noalloc_layout(nullptr, X.n, X.P, &B);
+  if (need > (size_t)FSQR_NOALLOC_SCRATCH_BYTES)
+    return fail(ctx, FSQR_EINVAL,
+                "n = %lld, P = %lld need %zu bytes of scratch; the static scratch holds %d "
+                "(FSQR_NOALLOC_SCRATCH_BYTES): use fsqr_lambda_max",
+                (long long)X.n, (long long)X.P, need, FSQR_NOALLOC_SCRATCH_BYTES);
+  unsigned char *base = nullptr;
+  TRY(noalloc_base(ctx, &base));
+  noalloc_layout(base, X.n, X.P, &B);
+  cudaStream_t st = ctx->stream;
+  // The array still holds the previous call's bytes. Every buffer below is
+  // fully written before it is read except the missing-entry counter, which
+  // k_col_stats increments: it must start at zero.
+  CK(cudaMemsetAsync(B.miss, 0, sizeof(int), st));
+  LK(launch_col_stats(X, B.mean, B.sd, B.miss, st));
+  const double *mean = d->col_mean ? d->col_mean : B.mean;
+  const double *sd = d->col_sd ? d->col_sd : B.sd;
+  LK(launch_affine(X, mean, sd, d->standardize, B.a, B.b, st));
+  X.a = B.a;
+  X.b = B.b;
+  int hmiss = 0;
+  CK(cudaMemcpyAsync(&hmiss, B.miss, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hmiss > 0)
+    return fail(ctx, FSQR_EINVAL,
+                "%d missing genotype entries: mean imputation of missing entries is not "
+                "supported by this build",
+                hmiss);
+  const int64_t n = X.n, npad = pad16(n);
+  int64_t k = (int64_t)ceil((double)n * tau);
+  if (k < 1) k = 1;
+  if (k > n) k = n;
+  LK(launch_select(y, n, k, B.q, st));
+  LK(launch_lmax_vec(y, n, npad, tau, B.q, B.v, st));
+  LK(launch_sum_cols(B.v, n, npad, 1, B.vs, nullptr, st));
+  Fits F = pass_fits(ctx, X);
+  LK(launch_col_pass(A_XT, 1, X, F, 0, B.v, B.vs, B.s, nullptr, st));
+  LK(launch_colmax_ratio(B.s, omega, X.P, (double)n, B.o, st));
+  CK(cudaMemcpyAsync(out, B.o, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return FSQR_OK;
 }
 

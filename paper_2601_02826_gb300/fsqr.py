@@ -62,7 +62,8 @@ class Profile(C.Structure):
 EXPORTS = ["fsqr_version", "fsqr_opts_default", "fsqr_create", "fsqr_destroy", "fsqr_last_error",
            "fsqr_col_stats", "fsqr_lambda_max", "fsqr_eta", "fsqr_fit", "fsqr_fit_batch",
            "fsqr_fit_batch_host", "fsqr_kkt", "fsqr_predict", "fsqr_back_transform",
-           "fsqr_profile_enable", "fsqr_profile_get", "fsqr_profile_reset"]
+           "fsqr_profile_enable", "fsqr_profile_get", "fsqr_profile_reset",
+           "fsqr_lambda_max_noalloc"]
 
 _lib = None
 
@@ -92,6 +93,7 @@ def load(path: str | None = None):
     L.fsqr_last_error.restype = C.c_char_p
     L.fsqr_col_stats.argtypes = [vp, pD, vp, vp]
     L.fsqr_lambda_max.argtypes = [vp, pD, vp, dbl, vp, pd]
+    L.fsqr_lambda_max_noalloc.argtypes = [vp, pD, vp, dbl, vp, pd]
     L.fsqr_eta.argtypes = [vp, pD, pi64, i32, dbl, dbl, i32, dbl, pd]
     L.fsqr_fit.argtypes = [vp, pD, vp, dbl, dbl, vp, pi64, i32, pO, vp, vp, vp, pI]
     L.fsqr_fit_batch.argtypes = [vp, pD, vp, i32, pd, i32, pd, vp, pi64, i32, pO, vp, vp, vp, pI]
@@ -192,6 +194,14 @@ class Context:
     def lambda_max(self, d, y, tau, omega) -> float:
         out = C.c_double()
         self._check(self.L.fsqr_lambda_max(self.h, C.byref(d), _ptr(y), tau, _ptr(omega), C.byref(out)))
+        return out.value
+
+    def lambda_max_noalloc(self, d, y, tau, omega) -> float:
+        """fsqr_lambda_max_noalloc: as lambda_max, on the library's static
+        device scratch instead of its workspace (no device allocation)."""
+        out = C.c_double()
+        self._check(self.L.fsqr_lambda_max_noalloc(self.h, C.byref(d), _ptr(y), tau, _ptr(omega),
+                                                   C.byref(out)))
         return out.value
 
     def eta(self, d, block_ptr, mu, margin=0.05, max_iter=100, tol=1e-6) -> np.ndarray:
