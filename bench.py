@@ -283,8 +283,9 @@ def run_gb300(args, rank, world, local_rank):
                      "kernel": "k_col_tc (column pass: X~^T theta on tcgen05 + beta prox)",
                      "bytes_per_launch": prof.col_bytes, "avg_launch_ms": col_avg_ms,
                      "samples": prof.col_samples, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
-        "kernels_ms": {"col": col_avg_ms, "xbeta": prof.xb_ms / max(1, prof.xb_samples),
-                       "vec": prof.vec_ms / max(1, prof.vec_samples)},
+        "kernels_ms": {"col": col_avg_ms,
+                       "xbeta_and_vector_update": prof.xb_ms / max(1, prof.xb_samples),
+                       "vec": (prof.vec_ms / prof.vec_samples) if prof.vec_samples else None},
         "iters": iters, "kkt": kkts, "iterations_timed": prof.iterations,
         "gpu_launches": int(prof.kernel_launches),
         "clocks": clocks.summary(),

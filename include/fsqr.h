@@ -230,8 +230,11 @@ int fsqr_back_transform(fsqr_ctx *ctx, const fsqr_design *X, const double *beta_
  * counts every kernel the library launched (graph replays included). */
 typedef struct {
   int64_t col_samples;  double col_ms;   /* column pass: X~^T theta + beta prox */
-  int64_t xb_samples;   double xb_ms;    /* X~ beta over the active columns */
-  int64_t vec_samples;  double vec_ms;   /* z, r, theta update */
+  int64_t xb_samples;   double xb_ms;    /* X~ beta over the active columns; on the
+                                            tensor-core path it includes the z, r,
+                                            theta update, fused into that pass */
+  int64_t vec_samples;  double vec_ms;   /* z, r, theta update (separate kernel only
+                                            off the tensor-core path) */
   int64_t iterations;                    /* FS-QRPPA steps executed */
   int64_t kernel_launches;
   int64_t col_bytes;                     /* algorithmic bytes of the last column pass */

@@ -549,6 +549,8 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     const int64_t maxkb = (P + 127) / 128;
     TRY(wsget(ctx, "g_scol", (size_t)(maxkb * 128), &scol));
     TRY(wsget(ctx, "g_wtile", (size_t)(maxkb * xbeta_tc_rows(NB) * 128), &wtile));
+    TRY(wsget(ctx, "g_xbtick", (size_t)((n + 127) / 128), &F.xb_tick));
+    CK(cudaMemsetAsync(F.xb_tick, 0, sizeof(unsigned) * (size_t)((n + 127) / 128), st));
     const size_t smem = col_tc_smem(NB, F.D, F.T);
     if (smem > 200 * 1024)
       return fail(ctx, FSQR_EINVAL, "tensor-core column pass needs %zu B of shared memory", smem);
@@ -589,7 +591,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     }
   }
   LK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, F.beta[0], st));
-  if (tc) LK(launch_xbeta_tc(NB, X, F, 0, F.beta[0], tmG, scol, wtile, d_err, st));
+  if (tc) LK(launch_xbeta_tc(NB, X, F, 0, 0, F.beta[0], tmG, scol, wtile, d_err, ctx->num_sms, st));
   else LK(launch_xbeta(NB, X, F, 0, F.beta[0], st));
   LK(launch_vec(NB, X, F, 0, 1, st));
 
@@ -599,10 +601,14 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   const bool prof = ctx->prof;
   if (prof && !ctx->ev[0])
     for (int e = 0; e < 6; ++e) CK(cudaEventCreate(&ctx->ev[e]));
+  // kernels per step: [quantize] col [check] (xprep + fused xbeta/vector | xbeta + vec)
   int per_graph = 1;  // the advance kernel
-  for (int off = 0; off < M; ++off) per_graph += 3 + (mixed ? 1 : 0) + (tc ? 1 : 0) + (off % K == 0 ? 1 : 0);
+  for (int off = 0; off < M; ++off) per_graph += (mixed ? 1 : 0) + 3 + (off % K == 0 ? 1 : 0);
   // Enqueues steps base..base+M-1 (kernels read the base from it_base); with
-  // sample set, events bracket the kernels of the last step.
+  // sample set, events bracket the kernels of the last step. The stop test of
+  // w^k reads only the column pass of step k and the vector pass of step k-1,
+  // so it runs before the X~ beta pass, which on the tensor-core path also
+  // applies the vector update.
   auto enqueue = [&](bool sample) -> cudaError_t {
     cudaError_t ce = cudaSuccess;
     for (int off = 0; off < M && ce == cudaSuccess; ++off) {
@@ -616,13 +622,13 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
         ce = launch_col_pass(A_PROX, NB, X, F, off, nullptr, nullptr, nullptr, nullptr, st);
       }
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[1], st);
-      if (ce == cudaSuccess)
-        ce = tc ? launch_xbeta_tc(NB, X, F, off, nullptr, tmG, scol, wtile, d_err, st)
-                : launch_xbeta(NB, X, F, off, nullptr, st);
-      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], st);
       if (off % K == 0 && ce == cudaSuccess) ce = launch_check(NB, F, off, st);
+      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], st);
+      if (ce == cudaSuccess)
+        ce = tc ? launch_xbeta_tc(NB, X, F, off, 1, nullptr, tmG, scol, wtile, d_err, ctx->num_sms, st)
+                : launch_xbeta(NB, X, F, off, nullptr, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[3], st);
-      if (ce == cudaSuccess) ce = launch_vec(NB, X, F, off, 0, st);
+      if (!tc && ce == cudaSuccess) ce = launch_vec(NB, X, F, off, 0, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[4], st);
     }
     if (ce == cudaSuccess) ce = launch_advance(it_base, M, st);
@@ -665,14 +671,16 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     if (sample) {
       float a = 0.f, b = 0.f, c = 0.f;
       if (cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]) == cudaSuccess &&
-          cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]) == cudaSuccess &&
+          cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]) == cudaSuccess &&
           cudaEventElapsedTime(&c, ctx->ev[3], ctx->ev[4]) == cudaSuccess) {
         ctx->pf.col_ms += a;
         ctx->pf.col_samples += 1;
         ctx->pf.xb_ms += b;
         ctx->pf.xb_samples += 1;
-        ctx->pf.vec_ms += c;
-        ctx->pf.vec_samples += 1;
+        if (!tc) {  // the tensor-core path has no separate vector kernel
+          ctx->pf.vec_ms += c;
+          ctx->pf.vec_samples += 1;
+        }
       } else {
         cudaGetLastError();
       }

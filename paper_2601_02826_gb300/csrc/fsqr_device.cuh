@@ -87,11 +87,42 @@ __device__ void col_finalize(const Fits &F) {
   }
 }
 
-// Vector-kernel counterpart: totals of the partials of the iterate of the
-// given parity, tot_c[par][b*4 + q] (q: max |r|, max dist, sum theta,
-// max |theta|).
+// dist(t, d rho_tau(z)): {tau} for z > 0, {tau-1} for z < 0, [tau-1, tau] at 0.
+__device__ __forceinline__ double dist_pinball(double t, double z, double tau) {
+  if (z > 0.0) return fabs(t - tau);
+  if (z < 0.0) return fabs(t - (tau - 1.0));
+  return fmax(fmax(tau - 1.0 - t, t - tau), 0.0);
+}
+
+// One sample of one fit, given q = x~_i^T beta^{k+1} (with its rounding
+// bound qerr) and the old z, theta, r:
+//   z^{k+1} = (v - tau/(n mu))_+ - (-v - (1-tau)/(n mu))_+,  v = z^k + theta^k/mu
+//   r^{k+1} = q + z^{k+1} - y_i
+//   theta^{k+1} = theta^k - mu/(G+1) (2 r^{k+1} - r^k)
+// stores them at index ib and returns the stop-test partials of w^{k+1}.
+__device__ __forceinline__ void row_update(const Fits &F, int64_t ib, double tau, double nmu, double n,
+                                           double q, double qerr, double yi, double zo, double th,
+                                           double ro, double *p) {
+  const double v = zo + th / F.mu;
+  // eq. z_update
+  const double zn = fmax(v - tau / nmu, 0.0) - fmax(-v - (1.0 - tau) / nmu, 0.0);
+  // eq. fsppa_update, theta line: extrapolated dual step of size mu/(G+1)
+  const double rn = q + zn - yi;
+  const double tn = th - F.sigma * (2.0 * rn - ro);
+  F.z[ib] = zn;
+  F.theta[ib] = tn;
+  F.r[ib] = rn;
+  p[0] = fabs(rn) + qerr;
+  p[1] = dist_pinball(n * tn, zn, tau);
+  p[2] = tn;
+  p[3] = fabs(tn);
+}
+
+// Vector-pass counterpart: totals of the nparts per-CTA partials of the
+// iterate of the given parity, tot_c[par][b*4 + q] (q: max |r|, max dist,
+// sum theta, max |theta|). Called by the gridDim.x CTAs that wrote partials.
 template <int NB>
-__device__ void vec_finalize(const Fits &F, int par) {
+__device__ void vec_finalize(const Fits &F, int par, int nparts) {
   __shared__ unsigned s_ticket;
   __shared__ double s_red[kCPartials][256];
   __threadfence();
@@ -107,7 +138,7 @@ __device__ void vec_finalize(const Fits &F, int par) {
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     if (t < nt)
 #pragma unroll 4
-      for (int c = t; c < F.gridC; c += nt) {
+      for (int c = t; c < nparts; c += nt) {
         const double *p = cp + (c * NB + b) * kCPartials;
         a0 = fmax(a0, __ldcg(p + 0));
         a1 = fmax(a1, __ldcg(p + 1));

@@ -78,6 +78,7 @@ struct Fits {
   double *tot_a;      // NB * 3: max dist, constant term, max |a_j beta_j|
   int *a_pre;         // gridA + 1: exclusive prefix of a_cnt
   unsigned *tickets;  // [0] column pass, [1] vector kernel
+  unsigned *xb_tick;  // per 128-row tile: splits of the fused X~ beta pass done (tensor-core path)
   // per-fit status
   int *done;        // NB: iteration whose iterate is final, -1 while running
   int *n_done;      // counter of finished fits
@@ -122,8 +123,11 @@ cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, c
                           const uint8_t *dgt, int grid, int tiles_per_cta, int *err,
                           cudaStream_t s);
 cudaError_t launch_tile_x(const Dsg &X, uint8_t *xt, int64_t nk, cudaStream_t s);
-cudaError_t launch_xbeta_tc(int NB, const Dsg &X, const Fits &F, int off, const double *beta_in,
-                            const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err, cudaStream_t s);
+// fuse = 1: the same launch also runs the vector update (k_vec) of the
+// iterate; fuse = 0: it leaves the integer partials for k_vec.
+cudaError_t launch_xbeta_tc(int NB, const Dsg &X, const Fits &F, int off, int fuse, const double *beta_in,
+                            const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err, int num_sms,
+                            cudaStream_t s);
 int xbeta_tc_rows(int NB);
 cudaError_t launch_quantize_tc(int NB, int D, const Fits &F, int off, uint8_t *dg, cudaStream_t s);
 size_t col_tc_smem(int NB, int D, int T);

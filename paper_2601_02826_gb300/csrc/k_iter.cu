@@ -58,12 +58,6 @@ __device__ __forceinline__ double dist_l1(double s, double lam, double b) {
   return fmax(fabs(s) - lam, 0.0);
 }
 
-// dist(t, d rho_tau(z)): {tau} for z > 0, {tau-1} for z < 0, [tau-1, tau] at 0.
-__device__ __forceinline__ double dist_pinball(double t, double z, double tau) {
-  if (z > 0.0) return fabs(t - tau);
-  if (z < 0.0) return fabs(t - (tau - 1.0));
-  return fmax(fmax(tau - 1.0 - t, t - tau), 0.0);
-}
 
 // Value of stored column entry (generic path, one sample).
 __device__ __forceinline__ double stored_value(const Dsg &X, const uint8_t *col, int64_t i) {
@@ -961,20 +955,8 @@ __global__ void __launch_bounds__(kCThreads) k_vec(Dsg X, Fits F, int off, int i
         p[b][2] = ti;
         p[b][3] = fabs(ti);
       } else {
-        const double zo = F.z[ib], th = F.theta[ib], ro = F.r[ib];
-        const double v = zo + th / F.mu;
-        // eq. z_update
-        const double zn = fmax(v - tau / nmu, 0.0) - fmax(-v - (1.0 - tau) / nmu, 0.0);
-        // eq. fsppa_update, theta line: extrapolated dual step of size mu/(G+1)
-        const double rn = xb[b] + zn - yi;
-        const double tn = th - F.sigma * (2.0 * rn - ro);
-        F.z[ib] = zn;
-        F.theta[ib] = tn;
-        F.r[ib] = rn;
-        p[b][0] = fabs(rn) + xb_err[b];
-        p[b][1] = dist_pinball((double)nrows * tn, zn, tau);
-        p[b][2] = tn;
-        p[b][3] = fabs(tn);
+        row_update(F, ib, tau, nmu, (double)nrows, xb[b], xb_err[b], yi, F.z[ib], F.theta[ib], F.r[ib],
+                   p[b]);
       }
     }
   }
@@ -992,7 +974,7 @@ __global__ void __launch_bounds__(kCThreads) k_vec(Dsg X, Fits F, int off, int i
     }
     __syncthreads();
   }
-  vec_finalize<NB>(F, par);
+  vec_finalize<NB>(F, par, F.gridC);
 }
 
 cudaError_t launch_vec(int NB, const Dsg &X, const Fits &F, int off, int init, cudaStream_t s) {

@@ -431,7 +431,7 @@ constexpr int kXTMaxSplits = 16;
 
 template <int NB, int DWD>
 __global__ void __launch_bounds__(128)
-    k_xprep(Dsg X, Fits F, int off, const double *__restrict__ beta_in, int *__restrict__ scol,
+    k_xprep(Dsg X, Fits F, int off, const double *__restrict__ beta_in, int split_cap, int *__restrict__ scol,
             uint8_t *__restrict__ wtile) {
   using Sh = XbShape<NB, DWD>;
   extern __shared__ int spre[];  // gridA + 1
@@ -445,7 +445,8 @@ __global__ void __launch_bounds__(128)
   const int A = __ldcg(F.a_pre + gA);
   const int nkb = (A + 127) / 128;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    F.meta_i[0] = max(1, min(kXTMaxSplits, nkb));
+    // splits of the X~ beta pass: enough CTAs for one resident wave
+    F.meta_i[0] = max(1, min(kXTMaxSplits, min(nkb, split_cap)));
     F.meta_i[1] = A;
   }
   if (threadIdx.x < NB) {
@@ -460,48 +461,55 @@ __global__ void __launch_bounds__(128)
       F.meta_d[kMaxNB + b] = scale;
     }
   }
-  if (blockIdx.x >= nkb) return;
+  if ((int)blockIdx.x >= nkb) return;
   for (int t = threadIdx.x; t <= gA; t += 128) spre[t] = __ldcg(F.a_pre + t);
   __syncthreads();
-  const int a = blockIdx.x * 128 + threadIdx.x;
-  int j = -1;
-  if (a < A) {
-    int lo = 0, hi = gA;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (spre[mid] <= a) lo = mid; else hi = mid;
-    }
-    j = F.a_list[(int64_t)lo * F.T + (a - spre[lo])];
-    if (j <= X.c) j = -1;  // covariates are summed in FP64 by k_vec
-  }
-  scol[a] = (j >= 0) ? (int)(j - 1 - X.c) : (int)X.p;
-  uint8_t *tile = wtile + (int64_t)blockIdx.x * Sh::B_BYTES;
   const int t = threadIdx.x, ch = t >> 4, bt = t & 15;
-  const double aj = (j >= 0) ? __ldg(X.a + j) : 0.0;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    long long W = (j >= 0) ? __double2ll_rn(aj * beta[(int64_t)j * NB + b] * sInv[b]) : 0;
-    int dig[DWD];
-#pragma unroll
-    for (int d = DWD - 1; d >= 1; --d) {
-      const int tt = (int)(((W + 8) & 15) - 8);
-      dig[d] = tt;
-      W = (W - tt) >> 4;
+  for (int kb = blockIdx.x; kb < nkb; kb += gridDim.x) {
+    const int a = kb * 128 + t;
+    int j = -1;
+    if (a < A) {
+      int lo = 0, hi = gA;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (spre[mid] <= a) lo = mid; else hi = mid;
+      }
+      j = F.a_list[(int64_t)lo * F.T + (a - spre[lo])];
+      if (j <= X.c) j = -1;  // covariates are summed in FP64 by the vector update
     }
-    dig[0] = (int)W;
+    scol[a] = (j >= 0) ? (int)(j - 1 - X.c) : (int)X.p;
+    uint8_t *tile = wtile + (int64_t)kb * Sh::B_BYTES;
+    const double aj = (j >= 0) ? __ldg(X.a + j) : 0.0;
 #pragma unroll
-    for (int d = 0; d < DWD; ++d) {
-      const int r = b * DWD + d;
-      tile[r * 128 + ((ch ^ (r & 7)) << 4) + bt] = kE4M3Int[dig[d] + 8];
+    for (int b = 0; b < NB; ++b) {
+      long long W = (j >= 0) ? __double2ll_rn(aj * beta[(int64_t)j * NB + b] * sInv[b]) : 0;
+      int dig[DWD];
+#pragma unroll
+      for (int d = DWD - 1; d >= 1; --d) {
+        const int tt = (int)(((W + 8) & 15) - 8);
+        dig[d] = tt;
+        W = (W - tt) >> 4;
+      }
+      dig[0] = (int)W;
+#pragma unroll
+      for (int d = 0; d < DWD; ++d) {
+        const int r = b * DWD + d;
+        tile[r * 128 + ((ch ^ (r & 7)) << 4) + bt] = kE4M3Int[dig[d] + 8];
+      }
     }
+    // digit rows beyond NB*DWD are zero
+    for (int r = NB * DWD; r < Sh::N; ++r) tile[r * 128 + ((ch ^ (r & 7)) << 4) + bt] = 0;
   }
-  // digit rows beyond NB*DWD are zero
-  for (int r = NB * DWD; r < Sh::N; ++r) tile[r * 128 + ((ch ^ (r & 7)) << 4) + bt] = 0;
 }
 
+// CTA (rt, sp). With fuse = 1 the last split CTA to finish a row tile sums
+// the splits' integer partials of its 128 rows and applies the vector update
+// (z, r, theta and the stop-test partials, as k_vec), and the last row tile
+// to finish writes the totals; the operands of that update that do not
+// depend on this pass are loaded before the pipeline drains.
 template <int NB, int DWD>
 __global__ void __launch_bounds__(128)
-    k_xbeta_tc(Dsg X, Fits F, const int *__restrict__ scol, const uint8_t *__restrict__ wtile,
+    k_xbeta_tc(Dsg X, Fits F, int off, int fuse, const int *__restrict__ scol, const uint8_t *__restrict__ wtile,
                const __grid_constant__ CUtensorMap tmX, int *err) {
   using Sh = XbShape<NB, DWD>;
   constexpr int N = Sh::N;
@@ -509,6 +517,8 @@ __global__ void __launch_bounds__(128)
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[ST], empty[ST], dbar;
   __shared__ uint32_t tmem_base;
+  __shared__ int s_last;
+  __shared__ double red[kCPartials][256];
   const uint32_t base_u32 = smem_u32(smem_raw);
   uint8_t *ring = smem_raw + (((base_u32 + 1023u) & ~1023u) - base_u32);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -517,98 +527,193 @@ __global__ void __launch_bounds__(128)
   const int S = F.meta_i[0];
   if ((int)blockIdx.y >= S) return;
   const int kb0 = (int)((int64_t)nkb * blockIdx.y / S), kb1 = (int)((int64_t)nkb * (blockIdx.y + 1) / S);
+  const bool has = kb1 > kb0;
   const int64_t i0 = (int64_t)blockIdx.x * 128;
+  const int64_t i = i0 + tid;
+  const bool row = i < F.n;
   long long *out = F.xb_ipart + (int64_t)blockIdx.y * F.npad * NB;
-  if (kb1 <= kb0) {
-    const int64_t i = i0 + tid;
-    if (i < F.npad)
+
+  // operands of the fused vector update (independent of this pass)
+  const int k = fuse ? (*F.it_base + off) : 0;
+  bool run[NB];
+  double yi = 0.0, zo[NB], th[NB], ro[NB], cv[NB];
 #pragma unroll
-      for (int b = 0; b < NB; ++b) out[i * NB + b] = 0;
-    return;
+  for (int b = 0; b < NB; ++b) { zo[b] = th[b] = ro[b] = cv[b] = 0.0; run[b] = false; }
+  if (fuse) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) run[b] = (b < F.nb) && (F.done[b] < 0);
+    if (row) {
+      yi = __ldg(F.y + i);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        zo[b] = F.z[i * NB + b];
+        th[b] = F.theta[i * NB + b];
+        ro[b] = F.r[i * NB + b];
+      }
+      const double *bt = F.beta[(k & 1) ^ 1];
+#pragma unroll 4
+      for (int64_t j = 1; j <= X.c; ++j) {
+        const double x = __ldg(X.cov + (j - 1) * X.n + i), aj = __ldg(X.a + j);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) cv[b] = fma(aj * __ldg(bt + j * NB + b), x, cv[b]);
+      }
+    }
   }
-  if (tid == 0) {
-    for (int q = 0; q < ST; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
-    mbar_init(&dbar, 1);
-    fence_mbar_init();
-  }
-  if (warp == 0) tmem_alloc(&tmem_base, Sh::TMEM_COLS);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_base;
-  if (warp == 0) {
-    // warp 0 streams the blocks: lane l gathers active columns 4l..4l+3 of
-    // a block; lane 0 also loads the digit tile and issues the MMAs
-    const int lane = tid & 31;
-    const uint32_t idesc = idesc_f32acc_amn(0u, 128u, (uint32_t)N);
-    const int nb = kb1 - kb0;
-    bool ok = true;
-    for (int it = 0; it < nb + ST; ++it) {
-      if (it < nb) {
-        const int s = it % ST;
-        const uint32_t ph = (uint32_t)(it / ST) & 1u;
-        int okl = 1;
-        if (lane == 0) {
-          okl = mbar_wait(&empty[s], ph ^ 1u, err, kErrEmpty) ? 1 : 0;
-          if (okl) {
-            mbar_arrive_expect_tx(&full[s], Sh::BUF);
-            bulk_load(ring + s * Sh::BUF + Sh::A_BYTES, wtile + (int64_t)(kb0 + it) * Sh::B_BYTES, Sh::B_BYTES,
-                      &full[s]);
+
+  long long V[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) V[b] = 0;
+  if (has) {
+    if (tid == 0) {
+      for (int q = 0; q < ST; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
+      mbar_init(&dbar, 1);
+      fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, Sh::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    if (warp == 0) {
+      // warp 0 streams the blocks: lane l gathers active columns 4l..4l+3 of
+      // a block (its column indices loaded one block ahead); lane 0 also
+      // loads the digit tile and issues the MMAs
+      const int lane = tid & 31;
+      const uint32_t idesc = idesc_f32acc_amn(0u, 128u, (uint32_t)N);
+      const int nb = kb1 - kb0;
+      bool ok = true;
+      int4 c4n = __ldg(reinterpret_cast<const int4 *>(scol + (int64_t)kb0 * 128) + lane);
+      for (int it = 0; it < nb + ST; ++it) {
+        if (it < nb) {
+          const int4 c4 = c4n;
+          if (it + 1 < nb) c4n = __ldg(reinterpret_cast<const int4 *>(scol + (int64_t)(kb0 + it + 1) * 128) + lane);
+          const int s = it % ST;
+          const uint32_t ph = (uint32_t)(it / ST) & 1u;
+          int okl = 1;
+          if (lane == 0) {
+            okl = mbar_wait(&empty[s], ph ^ 1u, err, kErrEmpty) ? 1 : 0;
+            if (okl) {
+              mbar_arrive_expect_tx(&full[s], Sh::BUF);
+              bulk_load(ring + s * Sh::BUF + Sh::A_BYTES, wtile + (int64_t)(kb0 + it) * Sh::B_BYTES, Sh::B_BYTES,
+                        &full[s]);
+            }
+          }
+          okl = __shfl_sync(0xffffffffu, okl, 0);
+          if (!okl) { ok = false; break; }
+          tma_gather4(ring + s * Sh::BUF + lane * 512, &tmX, &full[s], (int)i0, c4.x, c4.y, c4.z, c4.w);
+        }
+        const int mt = it - (ST - 1);
+        if (lane == 0 && mt >= 0 && mt < nb) {
+          const int s = mt % ST;
+          const uint32_t ph = (uint32_t)(mt / ST) & 1u;
+          if (!mbar_wait(&full[s], ph, err, kErrFull)) {
+            ok = false;
+          } else {
+            tc_fence_after();
+            const uint32_t sa = smem_u32(ring + s * Sh::BUF);
+            const uint64_t ad = sdesc_mn128(sa), bd = sdesc_k128(sa + Sh::A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma_f8(tmem, ad + (uint64_t)(kk * 256), bd + (uint64_t)(kk * 2), idesc, (mt | kk) != 0 ? 1u : 0u);
+            mma_commit(&empty[s]);
           }
         }
-        okl = __shfl_sync(0xffffffffu, okl, 0);
-        if (!okl) { ok = false; break; }
-        const int4 c4 = __ldg(reinterpret_cast<const int4 *>(scol + (int64_t)(kb0 + it) * 128) + lane);
-        tma_gather4(ring + s * Sh::BUF + lane * 512, &tmX, &full[s], (int)i0, c4.x, c4.y, c4.z, c4.w);
+        if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
       }
-      const int mt = it - (ST - 1);
-      if (lane == 0 && mt >= 0 && mt < nb) {
-        const int s = mt % ST;
-        const uint32_t ph = (uint32_t)(mt / ST) & 1u;
-        if (!mbar_wait(&full[s], ph, err, kErrFull)) {
-          ok = false;
-        } else {
-          tc_fence_after();
-          const uint32_t sa = smem_u32(ring + s * Sh::BUF);
-          const uint64_t ad = sdesc_mn128(sa), bd = sdesc_k128(sa + Sh::A_BYTES);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            mma_f8(tmem, ad + (uint64_t)(kk * 256), bd + (uint64_t)(kk * 2), idesc, (mt | kk) != 0 ? 1u : 0u);
-          mma_commit(&empty[s]);
-        }
-      }
-      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+      if (lane == 0) mma_commit(&dbar);
     }
-    if (lane == 0) mma_commit(&dbar);
-  }
-  __syncwarp();
-  const bool done = mbar_wait(&dbar, 0u, err, kErrAccFull);
-  tc_fence_after();
-  // epilogue: TMEM lane = sample row, columns b*DWD + d
-  {
+    __syncwarp();
+    const bool done = mbar_wait(&dbar, 0u, err, kErrAccFull);
+    tc_fence_after();
+    // TMEM lane = sample row, columns b*DWD + d
     uint32_t r[N];
 #pragma unroll
     for (int c = 0; c < N / 16; ++c) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * c), r + 16 * c);
     tmem_wait_ld();
-    const int64_t i = i0 + tid;
-    if (i < F.npad && done)
+    if (done)
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        long long V = 0;
+        long long v = 0;
 #pragma unroll
         for (int d = 0; d < DWD; ++d) {
           const float f = __uint_as_float(r[b * DWD + d]) * 512.0f;
-          V = V * 16 + (long long)__float2int_rn(f);
+          v = v * 16 + (long long)__float2int_rn(f);
         }
-        out[i * NB + b] = V;
+        V[b] = v;
       }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tc_fence_after();
+      tmem_dealloc(tmem, Sh::TMEM_COLS);
+    }
   }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tmem_dealloc(tmem, Sh::TMEM_COLS);
+  if (!fuse || S > 1) {
+    if (i < F.npad)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) out[i * NB + b] = V[b];
   }
+  if (!fuse) return;
+
+  // ---- fused vector update: the last split CTA of this row tile
+  if (S > 1) {
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&F.xb_tick[blockIdx.x], 1u) == (unsigned)(S - 1)) ? 1 : 0;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (row) {
+      // all split partials are loaded before any is added
+      for (int sp0 = 0; sp0 < S; sp0 += 8) {
+        long long v[8][NB];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const long long *src = F.xb_ipart + ((int64_t)(sp0 + u) * F.npad + i) * NB;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) v[u][b] = (sp0 + u < S) ? __ldcg(src + b) : 0;
+        }
+        if (sp0 == 0)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) V[b] = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) V[b] += v[u][b];
+      }
+    }
+    if (tid == 0) F.xb_tick[blockIdx.x] = 0u;
+  }
+  double p[NB][kCPartials];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int q = 0; q < kCPartials; ++q) p[b][q] = 0.0;
+  if (row) {
+    const double nmu = (double)F.n * F.mu;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (!run[b]) continue;
+      const double unit = F.meta_d[kMaxNB + b] * F.xb_unit;
+      const double q = F.meta_d[b] + (double)V[b] * unit + cv[b];
+      row_update(F, i * NB + b, F.tau[b], nmu, (double)F.n, q, (double)A * unit, yi, zo[b], th[b], ro[b], p[b]);
+    }
+  }
+  const int par = (k + 1) & 1;
+  const int ops[4] = {0, 0, 1, 0};
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+#pragma unroll
+    for (int q = 0; q < kCPartials; ++q) red[q][tid] = p[b][q];
+    __syncthreads();
+    tree_reduce<4>(red, ops, 128);
+    if (tid == 0 && run[b]) {
+      double *cp = F.c_part[par] + (blockIdx.x * NB + b) * kCPartials;
+      cp[0] = red[0][0]; cp[1] = red[1][0]; cp[2] = red[2][0]; cp[3] = red[3][0];
+    }
+    __syncthreads();
+  }
+  vec_finalize<NB>(F, par, (int)gridDim.x);
 }
 
 template <int NB, int DWD>
@@ -620,8 +725,8 @@ size_t xbeta_tc_smem(int NB, int DWD) {
 }
 
 template <int NB, int DWD>
-static cudaError_t xbeta_tc_t(const Dsg &X, const Fits &F, int off, const double *beta_in,
-                              const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err,
+static cudaError_t xbeta_tc_t(const Dsg &X, const Fits &F, int off, int fuse, const double *beta_in,
+                              const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err, int num_sms,
                               cudaStream_t s) {
   const size_t smem = xbeta_tc_smem(NB, DWD);
   if (smem > g_xt_opted<NB, DWD>) {
@@ -629,25 +734,35 @@ static cudaError_t xbeta_tc_t(const Dsg &X, const Fits &F, int off, const double
     if (e != cudaSuccess) return e;
     g_xt_opted<NB, DWD> = smem;
   }
-  // the prep grid covers every possible block of 128 active positions
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xbeta_tc<NB, DWD>, 128, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+  }
+  const int rows = (int)((X.n + 127) / 128);
+  const int split_cap = std::max(1, per_sm * num_sms / rows);
+  // the prep grid strides over the blocks of 128 active positions
   const int maxkb = (int)((X.P + 127) / 128);
+  const int pgrid = std::max(1, std::min(maxkb, num_sms));
   const size_t psmem = (size_t)(F.gridA + 1) * sizeof(int);
-  k_xprep<NB, DWD><<<maxkb, 128, psmem, s>>>(X, F, off, beta_in, scol, wtile);
+  k_xprep<NB, DWD><<<pgrid, 128, psmem, s>>>(X, F, off, beta_in, split_cap, scol, wtile);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)((X.n + 127) / 128), kXTMaxSplits);
-  k_xbeta_tc<NB, DWD><<<grid, 128, smem, s>>>(X, F, scol, wtile, tmX, err);
+  const dim3 grid((unsigned)rows, kXTMaxSplits);
+  k_xbeta_tc<NB, DWD><<<grid, 128, smem, s>>>(X, F, off, fuse, scol, wtile, tmX, err);
   return cudaGetLastError();
 }
 
 // scol: (P + 127)/128*128 ints; wtile: (P + 127)/128 tiles of N*128 bytes.
-cudaError_t launch_xbeta_tc(int NB, const Dsg &X, const Fits &F, int off, const double *beta_in,
-                            const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err, cudaStream_t s) {
+cudaError_t launch_xbeta_tc(int NB, const Dsg &X, const Fits &F, int off, int fuse, const double *beta_in,
+                            const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err, int num_sms,
+                            cudaStream_t s) {
   switch (NB) {
-    case 1: return xbeta_tc_t<1, 11>(X, F, off, beta_in, tmX, scol, wtile, err, s);
-    case 2: return xbeta_tc_t<2, 11>(X, F, off, beta_in, tmX, scol, wtile, err, s);
-    case 3: return xbeta_tc_t<3, 11>(X, F, off, beta_in, tmX, scol, wtile, err, s);
-    case 4: return xbeta_tc_t<4, 11>(X, F, off, beta_in, tmX, scol, wtile, err, s);
+    case 1: return xbeta_tc_t<1, 11>(X, F, off, fuse, beta_in, tmX, scol, wtile, err, num_sms, s);
+    case 2: return xbeta_tc_t<2, 11>(X, F, off, fuse, beta_in, tmX, scol, wtile, err, num_sms, s);
+    case 3: return xbeta_tc_t<3, 11>(X, F, off, fuse, beta_in, tmX, scol, wtile, err, num_sms, s);
+    case 4: return xbeta_tc_t<4, 11>(X, F, off, fuse, beta_in, tmX, scol, wtile, err, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }
