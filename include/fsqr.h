@@ -244,6 +244,49 @@ int fsqr_profile_enable(fsqr_ctx *ctx, int on);
 int fsqr_profile_get(fsqr_ctx *ctx, fsqr_profile *out);
 int fsqr_profile_reset(fsqr_ctx *ctx);
 
+/* ---- learned warm start ------------------------------------------------
+ * The paper warm-starts each fit of a lambda path from the previous
+ * solution (Section 7). The learned warm start extends that idea; the paper
+ * defines no network, so the definitions are this library's:
+ *   inputs of feature column j >= 1 of a fit (tau, lambda):
+ *     u_j = (tau, lambda / lambda_max(tau), x~_j^T v / (n lambda_max(tau))),
+ *     v_i = tau - 1{y_i < y_(ceil(n tau))}  (the direction of fsqr_lambda_max);
+ *   network: FSQR_MLP_IN -> 256 -> 256 -> 256 -> 1, ReLU on the hidden
+ *     layers, FP32 parameters, flat: W_0 (row-major d_0 x d_1), b_0, W_1,
+ *     b_1, W_2, b_2, W_3, b_3 (fsqr_mlp_param_count() floats);
+ *   start: beta_0 = y_(ceil(n tau)), beta_j = sd(y) f(u_j),
+ *     z = y - X~ beta, theta_i = (tau - 1{z_i < 0}) / n;
+ *   training: Adam (b1 0.9, b2 0.999, eps 1e-8, bias-corrected) on
+ *     sum_r w_r (f(u_r) - t_r)^2 / sum_r w_r over uniformly drawn batches.
+ * Solving from the start (fsqr_fit with FSQR_WARM_GIVEN) reaches the same
+ * stop test as a cold start; only the iteration count changes. All arrays
+ * are caller-owned device memory; rows x FSQR_MLP_IN inputs are row-major. */
+#define FSQR_MLP_IN 3
+int64_t fsqr_mlp_param_count(void);
+/* He-uniform weights U(-sqrt(6/fan_in), +) from splitmix64(seed + index), zero biases. */
+int fsqr_mlp_init(fsqr_ctx *ctx, float *params, uint64_t seed);
+/* out[r] = f(x_r), r < rows. */
+int fsqr_mlp_forward(fsqr_ctx *ctx, const float *params, const float *x, int64_t rows, float *out);
+/* grad (param-count floats) = gradient of the weighted loss over the rows;
+ * loss: host, may be NULL. 1 <= rows <= 2^24. */
+int fsqr_mlp_grad(fsqr_ctx *ctx, const float *params, const float *x, const float *t, const float *w,
+                  int64_t rows, float *grad, double *loss);
+/* `steps` Adam steps numbered step0+1 .. step0+steps (m, v: moment arrays
+ * of param-count floats, zero before the first step). Step k draws `batch`
+ * rows r_i = splitmix64(splitmix64(seed ^ k * 0xD1B54A32D192ED03) + i) mod rows.
+ * losses: host, `steps` batch losses, may be NULL. */
+int fsqr_mlp_train(fsqr_ctx *ctx, float *params, float *m, float *v, int64_t step0, const float *x,
+                   const float *t, const float *w, int64_t rows, int steps, int batch, float lr,
+                   uint64_t seed, double *losses);
+/* u: device, (P-1) x FSQR_MLP_IN inputs of one fit; lambda_max: host, may be NULL. */
+int fsqr_warm_features(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau,
+                       double lam_frac, const double *omega, float *u, double *lambda_max);
+/* The start proposed by the network for (tau, lambda_frac * lambda_max(tau)):
+ * beta (P), z (n), theta (n), device. */
+int fsqr_warm_start(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau,
+                    double lam_frac, const double *omega, const float *params, double *beta,
+                    double *z, double *theta);
+
 /* ---- lambda_max without device allocation -------------------------------
  * The paper has no counterpart: this entry point is a property of the
  * library, not of the method. It computes exactly what fsqr_lambda_max

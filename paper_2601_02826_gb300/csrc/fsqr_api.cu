@@ -119,35 +119,6 @@ int pinned(fsqr_ctx *ctx, size_t count, double **out) {
 
 int64_t pad16(int64_t n) { return (n + 15) / 16 * 16; }
 
-// 2-D uint8 TMA descriptor with the 128-byte swizzle and zero fill outside
-// the tensor: dim0 contiguous (bytes), dim1 rows of stride1 bytes.
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-int make_tmap_u8(fsqr_ctx *ctx, CUtensorMap *out, const void *base, uint64_t dim0, uint64_t dim1,
-                 uint64_t stride1, uint32_t box0, uint32_t box1) {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
-      return fail(ctx, FSQR_ECUDA, "cuTensorMapEncodeTiled is not available");
-    fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  const cuuint64_t dims[2] = {dim0, dim1};
-  const cuuint64_t strides[1] = {stride1};
-  const cuuint32_t box[2] = {box0, box1};
-  const cuuint32_t es[2] = {1, 1};
-  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(ctx, FSQR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-  return FSQR_OK;
-}
-
 int64_t col_bytes(int64_t n, int fmt) {
   if (fmt == FSQR_DENSE_F64) return 8 * n;
   if (fmt == FSQR_INT8) return n;
@@ -309,9 +280,14 @@ Fits pass_fits(fsqr_ctx *ctx, const Dsg &X) {
   return F;
 }
 
-// lambda_max(tau) for one tau (host result).
-int lambda_max_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, const double *omega,
-                    double *out) {
+// Device side of lambda_max(tau): q = y_(ceil(n tau)), s = X~^T v with
+// v_i = tau - 1{y_i < q}, and o = lambda_max, all left in the workspace.
+struct LmaxDev {
+  double *q, *s, *o;
+};
+
+int lambda_max_dev(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, const double *omega,
+                   LmaxDev *out) {
   const Dsg &X = pr.X;
   const int64_t n = X.n, npad = pad16(n);
   double *q, *v, *vs, *s, *o;
@@ -329,7 +305,16 @@ int lambda_max_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, 
   Fits F = pass_fits(ctx, X);
   LK(launch_col_pass(A_XT, 1, X, F, 0, v, vs, s, nullptr, ctx->stream));
   LK(launch_colmax_ratio(s, omega, X.P, (double)n, o, ctx->stream));
-  CK(cudaMemcpyAsync(out, o, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  *out = LmaxDev{q, s, o};
+  return FSQR_OK;
+}
+
+// lambda_max(tau) for one tau (host result).
+int lambda_max_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, const double *omega,
+                    double *out) {
+  LmaxDev L;
+  TRY(lambda_max_dev(ctx, pr, y, tau, omega, &L));
+  CK(cudaMemcpyAsync(out, L.o, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return FSQR_OK;
 }
@@ -455,8 +440,8 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   const int NB = nb_template(nb);
   const int64_t n = X.n, npad = pad16(n), P = X.P;
   const bool mixed = E.o->precision == FSQR_MIXED || E.o->precision == FSQR_MIXED_SIMT;
-  // tensor-core column pass: int8 storage, at most 63 covariates, <= 4 fits
-  const bool tc = E.o->precision == FSQR_MIXED && X.fmt == FSQR_INT8 && X.p > 0 && X.c <= 63 && NB <= 4;
+  // tensor-core column pass: int8 storage, at most 63 covariates, <= 8 fits
+  const bool tc = E.o->precision == FSQR_MIXED && X.fmt == FSQR_INT8 && X.p > 0 && X.c <= 63 && NB <= 8;
   const double t0 = now_ms();
   cudaStream_t st = ctx->stream;
 
@@ -490,13 +475,11 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   F.n4p = npad / 4;
   F.colbound = E.pr->colbound;
   // tiling from the occupancy of the kernel this group runs
-  int tc_grid = 0, tc_tpc = 0;
+  TcSchedule tsc{};
   if (tc) {
-    const int64_t tiles = (X.p + 127) / 128;
-    tc_grid = (int)std::min<int64_t>(tiles, ctx->num_sms);
-    tc_tpc = (int)((tiles + tc_grid - 1) / tc_grid);
-    F.T = 128 * tc_tpc + 64;  // tile columns, then up to 64 dense columns
-    F.gridA = tc_grid;
+    col_tc_schedule(X.p, n, ctx->num_sms, &tsc);
+    F.T = tsc.list_stride;  // whole-tile columns, then up to 64 dense columns
+    F.gridA = tsc.slots;
   } else {
     Fits tmp = F;
     tmp.T = 32;
@@ -531,7 +514,8 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   F.it_base = it_base;
   uint8_t *dg = nullptr, *xt = nullptr, *wtile = nullptr;
   int *d_err = nullptr, *scol = nullptr;
-  CUtensorMap tmG;
+  int32_t *tail_part = nullptr;
+  unsigned *tail_tick = nullptr;
   if (tc) {
     // tiled copy of X (byte image of the swizzled operand tiles) and the
     // tiled digit matrix, one 128 x N block per 128-sample chunk
@@ -544,13 +528,15 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     CK(cudaMemsetAsync(dg, 0, (size_t)(nk * N * 128), st));
     CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
     LK(launch_tile_x(X, xt, nk, st));
-    // rows of the stored matrix (one column each) for the gathered X~ beta
-    TRY(make_tmap_u8(ctx, &tmG, X.geno, (uint64_t)n, (uint64_t)X.p, (uint64_t)X.ld, 128, 1));
     const int64_t maxkb = (P + 127) / 128;
     TRY(wsget(ctx, "g_scol", (size_t)(maxkb * 128), &scol));
     TRY(wsget(ctx, "g_wtile", (size_t)(maxkb * xbeta_tc_rows(NB) * 128), &wtile));
     TRY(wsget(ctx, "g_xbtick", (size_t)((n + 127) / 128), &F.xb_tick));
     CK(cudaMemsetAsync(F.xb_tick, 0, sizeof(unsigned) * (size_t)((n + 127) / 128), st));
+    TRY(wsget(ctx, "g_tailpart", (size_t)std::max(1, tsc.rem * tsc.slices) * tc_tail_rows(NB, F.D) * 128,
+              &tail_part));
+    TRY(wsget(ctx, "g_tailtick", (size_t)std::max(1, tsc.rem), &tail_tick));
+    CK(cudaMemsetAsync(tail_tick, 0, sizeof(unsigned) * (size_t)std::max(1, tsc.rem), st));
     const size_t smem = col_tc_smem(NB, F.D, F.T);
     if (smem > 200 * 1024)
       return fail(ctx, FSQR_EINVAL, "tensor-core column pass needs %zu B of shared memory", smem);
@@ -591,7 +577,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     }
   }
   LK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, F.beta[0], st));
-  if (tc) LK(launch_xbeta_tc(NB, X, F, 0, 0, F.beta[0], tmG, scol, wtile, d_err, ctx->num_sms, st));
+  if (tc) LK(launch_xbeta_tc(NB, X, F, 0, 0, F.beta[0], scol, wtile, d_err, ctx->num_sms, st));
   else LK(launch_xbeta(NB, X, F, 0, F.beta[0], st));
   LK(launch_vec(NB, X, F, 0, 1, st));
 
@@ -617,7 +603,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
       else if (mixed) ce = launch_quantize(NB, F, off, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[0], st);
       if (tc) {
-        if (ce == cudaSuccess) ce = launch_col_tc(NB, F.D, X, F, off, xt, dg, tc_grid, tc_tpc, d_err, st);
+        if (ce == cudaSuccess) ce = launch_col_tc(NB, F.D, X, F, off, xt, dg, tsc, tail_part, tail_tick, d_err, st);
       } else if (ce == cudaSuccess) {
         ce = launch_col_pass(A_PROX, NB, X, F, off, nullptr, nullptr, nullptr, nullptr, st);
       }
@@ -625,7 +611,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
       if (off % K == 0 && ce == cudaSuccess) ce = launch_check(NB, F, off, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], st);
       if (ce == cudaSuccess)
-        ce = tc ? launch_xbeta_tc(NB, X, F, off, 1, nullptr, tmG, scol, wtile, d_err, ctx->num_sms, st)
+        ce = tc ? launch_xbeta_tc(NB, X, F, off, 1, nullptr, scol, wtile, d_err, ctx->num_sms, st)
                 : launch_xbeta(NB, X, F, off, nullptr, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[3], st);
       if (!tc && ce == cudaSuccess) ce = launch_vec(NB, X, F, off, 0, st);
@@ -907,6 +893,40 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
       if (worst == FSQR_OK && infos[f].status != FSQR_OK) worst = infos[f].status;
     }
   return worst;
+}
+
+// out[b*n + i] = x~_i^T beta_b for B coefficient vectors (FP64 path).
+int predict_impl(fsqr_ctx *ctx, const Prep &pr, const double *beta, int B, double *out) {
+  const Dsg &X = pr.X;
+  const int64_t n = X.n, npad = pad16(n), P = X.P;
+  cudaStream_t st = ctx->stream;
+  Fits F = pass_fits(ctx, X);
+  TRY(wsget(ctx, "p_xbpart", (size_t)kBMaxSplits * npad * kMaxNB, &F.xb_part));
+  TRY(wsget(ctx, "p_arb", (size_t)F.gridA * kMaxNB, &F.a_rb));
+  TRY(wsget(ctx, "p_act", (size_t)F.gridA * kMaxNB, &F.a_ct));
+  TRY(wsget(ctx, "p_acnt", (size_t)F.gridA, &F.a_cnt));
+  TRY(wsget(ctx, "p_alist", (size_t)F.gridA * F.T, &F.a_list));
+  TRY(wsget(ctx, "p_metai", 4, &F.meta_i));
+  TRY(wsget(ctx, "p_metad", 2 * kMaxNB, &F.meta_d));
+  TRY(alloc_totals(ctx, F, "p"));
+  int *done;
+  TRY(wsget(ctx, "p_done", kMaxNB, &done));
+  F.done = done;
+  CK(cudaMemsetAsync(done, 0xff, sizeof(int) * kMaxNB, st));
+  double *bg;
+  TRY(wsget(ctx, "p_bg", (size_t)P * kMaxNB, &bg));
+  CK(cudaMemsetAsync(bg, 0, sizeof(double) * P * kMaxNB, st));
+  for (int b0 = 0; b0 < B; b0 += kMaxNB) {
+    const int nb = std::min(kMaxNB, B - b0);
+    const int NB = nb_template(nb);
+    F.nb = nb;
+    LK(launch_pack(beta + (int64_t)b0 * P, P, bg, P, nb, NB, P, st));
+    LK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, bg, st));
+    LK(launch_xbeta(NB, X, F, 0, bg, st));
+    LK(launch_gather_xb(NB, F, out + (int64_t)b0 * n, n, nb, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return FSQR_OK;
 }
 
 }  // namespace
@@ -1207,36 +1227,7 @@ int fsqr_predict(fsqr_ctx *ctx, const fsqr_design *Xd, const double *beta, int B
   if (B == 0) return FSQR_OK;
   Prep pr;
   TRY(prepare(ctx, Xd, &pr, false));
-  const Dsg &X = pr.X;
-  const int64_t n = X.n, npad = pad16(n), P = X.P;
-  cudaStream_t st = ctx->stream;
-  Fits F = pass_fits(ctx, X);
-  TRY(wsget(ctx, "p_xbpart", (size_t)kBMaxSplits * npad * kMaxNB, &F.xb_part));
-  TRY(wsget(ctx, "p_arb", (size_t)F.gridA * kMaxNB, &F.a_rb));
-  TRY(wsget(ctx, "p_act", (size_t)F.gridA * kMaxNB, &F.a_ct));
-  TRY(wsget(ctx, "p_acnt", (size_t)F.gridA, &F.a_cnt));
-  TRY(wsget(ctx, "p_alist", (size_t)F.gridA * F.T, &F.a_list));
-  TRY(wsget(ctx, "p_metai", 4, &F.meta_i));
-  TRY(wsget(ctx, "p_metad", 2 * kMaxNB, &F.meta_d));
-  TRY(alloc_totals(ctx, F, "p"));
-  int *done;
-  TRY(wsget(ctx, "p_done", kMaxNB, &done));
-  F.done = done;
-  CK(cudaMemsetAsync(done, 0xff, sizeof(int) * kMaxNB, st));
-  double *bg;
-  TRY(wsget(ctx, "p_bg", (size_t)P * kMaxNB, &bg));
-  CK(cudaMemsetAsync(bg, 0, sizeof(double) * P * kMaxNB, st));
-  for (int b0 = 0; b0 < B; b0 += kMaxNB) {
-    const int nb = std::min(kMaxNB, B - b0);
-    const int NB = nb_template(nb);
-    F.nb = nb;
-    LK(launch_pack(beta + (int64_t)b0 * P, P, bg, P, nb, NB, P, st));
-    LK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, bg, st));
-    LK(launch_xbeta(NB, X, F, 0, bg, st));
-    LK(launch_gather_xb(NB, F, out + (int64_t)b0 * n, n, nb, st));
-  }
-  CK(cudaStreamSynchronize(st));
-  return FSQR_OK;
+  return predict_impl(ctx, pr, beta, B, out);
 }
 
 int fsqr_profile_enable(fsqr_ctx *ctx, int on) {
@@ -1265,6 +1256,178 @@ int fsqr_back_transform(fsqr_ctx *ctx, const fsqr_design *Xd, const double *beta
   Prep pr;
   TRY(prepare(ctx, Xd, &pr, false));
   LK(launch_back_transform(pr.X, beta_std, B, beta_out, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSQR_OK;
+}
+
+}  // extern "C"
+
+// ---- learned warm start ------------------------------------------------------
+
+namespace {
+
+// Work buffers of the network for `rows` inputs at a time.
+struct MlpWs {
+  float *H[kMlpLayers - 1];
+  float *G0, *G1, *f, *g;
+};
+
+int mlp_ws(fsqr_ctx *ctx, int64_t rows, MlpWs *w) {
+  const size_t hid = (size_t)rows * kMlpHidden;
+  TRY(wsget(ctx, "mlp_h0", hid, &w->H[0]));
+  TRY(wsget(ctx, "mlp_h1", hid, &w->H[1]));
+  TRY(wsget(ctx, "mlp_h2", hid, &w->H[2]));
+  TRY(wsget(ctx, "mlp_g0", hid, &w->G0));
+  TRY(wsget(ctx, "mlp_g1", hid, &w->G1));
+  TRY(wsget(ctx, "mlp_f", (size_t)rows, &w->f));
+  TRY(wsget(ctx, "mlp_g", (size_t)rows, &w->g));
+  return FSQR_OK;
+}
+
+constexpr int64_t kMlpChunk = 32768;  // inference rows per forward pass
+
+int mlp_forward_chunked(fsqr_ctx *ctx, const float *params, const float *x, int64_t rows, float *out) {
+  MlpWs w;
+  TRY(mlp_ws(ctx, std::min(rows, kMlpChunk), &w));
+  for (int64_t r0 = 0; r0 < rows; r0 += kMlpChunk) {
+    const int64_t nr = std::min(kMlpChunk, rows - r0);
+    LK(mlp_forward(params, x + r0 * kMlpIn, nr, w.H, out + r0, ctx->stream));
+  }
+  return FSQR_OK;
+}
+
+// The inputs u of every feature column of one fit (device, (P-1) x 3), with
+// the lambda_max pieces left on the device.
+int warm_features_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, double frac,
+                       const double *omega, float *u, LmaxDev *L) {
+  TRY(lambda_max_dev(ctx, pr, y, tau, omega, L));
+  LK(launch_warm_features(L->s, pr.X.P, pr.X.n, tau, frac, L->o, u, ctx->stream));
+  return FSQR_OK;
+}
+
+int check_warm_args(fsqr_ctx *ctx, const double *y, double tau, double frac, const double *omega) {
+  if (!y || !omega) return fail(ctx, FSQR_EINVAL, "NULL argument");
+  if (!(tau > 0.0 && tau < 1.0)) return fail(ctx, FSQR_EINVAL, "tau must be in (0,1)");
+  if (!(frac > 0.0)) return fail(ctx, FSQR_EINVAL, "lambda_frac must be > 0");
+  return FSQR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t fsqr_mlp_param_count(void) { return mlp_param_count(); }
+
+int fsqr_mlp_init(fsqr_ctx *ctx, float *params, uint64_t seed) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!params) return fail(ctx, FSQR_EINVAL, "NULL params");
+  int *dd;
+  TRY(wsget(ctx, "mlp_dims", kMlpLayers + 1, &dd));
+  LK(mlp_init(params, dd, seed, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSQR_OK;
+}
+
+int fsqr_mlp_forward(fsqr_ctx *ctx, const float *params, const float *x, int64_t rows, float *out) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!params || !x || !out || rows < 0) return fail(ctx, FSQR_EINVAL, "bad arguments");
+  if (rows == 0) return FSQR_OK;
+  TRY(mlp_forward_chunked(ctx, params, x, rows, out));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSQR_OK;
+}
+
+int fsqr_mlp_grad(fsqr_ctx *ctx, const float *params, const float *x, const float *t, const float *w,
+                  int64_t rows, float *grad, double *loss) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!params || !x || !t || !w || !grad || rows < 1) return fail(ctx, FSQR_EINVAL, "bad arguments");
+  if (rows > (int64_t)1 << 24) return fail(ctx, FSQR_EINVAL, "rows > 2^24");
+  MlpWs ws;
+  TRY(mlp_ws(ctx, rows, &ws));
+  double *dl;
+  TRY(wsget(ctx, "mlp_loss", 1, &dl));
+  LK(mlp_grad(params, x, t, w, rows, ws.H, ws.G0, ws.G1, ws.f, ws.g, grad, dl, ctx->stream));
+  double hl = 0.0;
+  CK(cudaMemcpyAsync(&hl, dl, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (loss) *loss = hl;
+  return FSQR_OK;
+}
+
+int fsqr_mlp_train(fsqr_ctx *ctx, float *params, float *m, float *v, int64_t step0, const float *x,
+                   const float *t, const float *w, int64_t rows, int steps, int batch, float lr,
+                   uint64_t seed, double *losses) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!params || !m || !v || !x || !t || !w || rows < 1 || steps < 0 || batch < 1 || step0 < 0 ||
+      !(lr > 0.f))
+    return fail(ctx, FSQR_EINVAL, "bad arguments");
+  if (batch > (1 << 20)) return fail(ctx, FSQR_EINVAL, "batch > 2^20");
+  if (steps == 0) return FSQR_OK;
+  MlpWs ws;
+  TRY(mlp_ws(ctx, batch, &ws));
+  float *xb, *tb, *wb, *grad;
+  double *dl;
+  const int64_t count = mlp_param_count();
+  TRY(wsget(ctx, "mlp_xb", (size_t)batch * kMlpIn, &xb));
+  TRY(wsget(ctx, "mlp_tb", (size_t)batch, &tb));
+  TRY(wsget(ctx, "mlp_wb", (size_t)batch, &wb));
+  TRY(wsget(ctx, "mlp_grad", (size_t)count, &grad));
+  TRY(wsget(ctx, "mlp_losses", (size_t)steps, &dl));
+  cudaStream_t st = ctx->stream;
+  for (int k = 0; k < steps; ++k) {
+    const int64_t step = step0 + k + 1;
+    LK(mlp_sample(x, t, w, rows, batch, seed, step, xb, tb, wb, st));
+    LK(mlp_grad(params, xb, tb, wb, batch, ws.H, ws.G0, ws.G1, ws.f, ws.g, grad, dl + k, st));
+    LK(mlp_adam(params, grad, m, v, count, step, lr, st));
+  }
+  if (losses) CK(cudaMemcpyAsync(losses, dl, sizeof(double) * steps, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return FSQR_OK;
+}
+
+int fsqr_warm_features(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, double tau, double lam_frac,
+                       const double *omega, float *u, double *lambda_max) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  TRY(check_warm_args(ctx, y, tau, lam_frac, omega));
+  if (!u) return fail(ctx, FSQR_EINVAL, "NULL output");
+  Prep pr;
+  TRY(prepare(ctx, Xd, &pr, false));
+  LmaxDev L;
+  TRY(warm_features_impl(ctx, pr, y, tau, lam_frac, omega, u, &L));
+  double h = 0.0;
+  CK(cudaMemcpyAsync(&h, L.o, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (lambda_max) *lambda_max = h;
+  return FSQR_OK;
+}
+
+int fsqr_warm_start(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, double tau, double lam_frac,
+                    const double *omega, const float *params, double *beta, double *z, double *theta) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  TRY(check_warm_args(ctx, y, tau, lam_frac, omega));
+  if (!params || !beta || !z || !theta) return fail(ctx, FSQR_EINVAL, "NULL argument");
+  Prep pr;
+  TRY(prepare(ctx, Xd, &pr, false));
+  const Dsg &X = pr.X;
+  double ymax = 0.0, ysd = 0.0;
+  TRY(y_stats(ctx, y, X.n, &ymax, &ysd));
+  float *u, *f;
+  double *xb;
+  TRY(wsget(ctx, "warm_u", (size_t)std::max<int64_t>(1, X.P - 1) * kMlpIn, &u));
+  TRY(wsget(ctx, "warm_f", (size_t)std::max<int64_t>(1, X.P - 1), &f));
+  TRY(wsget(ctx, "warm_xb", (size_t)X.n, &xb));
+  LmaxDev L;
+  TRY(warm_features_impl(ctx, pr, y, tau, lam_frac, omega, u, &L));
+  if (X.P > 1) TRY(mlp_forward_chunked(ctx, params, u, X.P - 1, f));
+  LK(launch_warm_beta(f, X.P, L.q, ysd, beta, ctx->stream));
+  TRY(predict_impl(ctx, pr, beta, 1, xb));
+  LK(launch_warm_dual(y, xb, X.n, tau, z, theta, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return FSQR_OK;
 }

@@ -118,20 +118,48 @@ cudaError_t launch_advance(int *it_base, int M, cudaStream_t s);
 cudaError_t launch_gather_xb(int NB, const Fits &F, double *out, int64_t ldo, int nb,
                              cudaStream_t s);  // out[b*ldo + i], i < F.n (FP64 path)
 
-// Tensor-core column pass (k_tc.cu).
+// Tensor-core column pass (k_tc.cu). Schedule: CTA c takes `rounds` whole
+// 128-column tiles (c, c + grid, ...); the rem tiles left over are cut into
+// `slices` sample slices each, computed by CTAs 0 .. rem*slices-1.
+struct TcSchedule {
+  int grid, rounds, rem, slices;
+  int list_stride;  // F.T: 128 * max(rounds, 1) + 64
+  int slots;        // F.gridA: grid + rem list slots
+};
+void col_tc_schedule(int64_t p, int64_t n, int num_sms, TcSchedule *out);
+int tc_tail_rows(int NB, int D);  // int32 digit sums per tail column and slice
 cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, const uint8_t *xt,
-                          const uint8_t *dgt, int grid, int tiles_per_cta, int *err,
-                          cudaStream_t s);
+                          const uint8_t *dgt, const TcSchedule &sc, int32_t *tail_part,
+                          unsigned *tail_tick, int *err, cudaStream_t s);
 cudaError_t launch_tile_x(const Dsg &X, uint8_t *xt, int64_t nk, cudaStream_t s);
 // fuse = 1: the same launch also runs the vector update (k_vec) of the
 // iterate; fuse = 0: it leaves the integer partials for k_vec.
 cudaError_t launch_xbeta_tc(int NB, const Dsg &X, const Fits &F, int off, int fuse, const double *beta_in,
-                            const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err, int num_sms,
-                            cudaStream_t s);
+                            int *scol, uint8_t *wtile, int *err, int num_sms, cudaStream_t s);
 int xbeta_tc_rows(int NB);
 cudaError_t launch_quantize_tc(int NB, int D, const Fits &F, int off, uint8_t *dg, cudaStream_t s);
 size_t col_tc_smem(int NB, int D, int T);
 int tc_rows(int NB, int D);
+
+// Learned warm start (k_mlp.cu): a 3 -> 256 -> 256 -> 256 -> 1 ReLU network
+// in FP32, flat parameters W_0, b_0, W_1, ... (W_l row-major d_l x d_{l+1}).
+constexpr int kMlpIn = 3, kMlpHidden = 256, kMlpLayers = 4;
+int64_t mlp_param_count();
+cudaError_t mlp_forward(const float *params, const float *x, int64_t rows, float *const *H, float *out,
+                        cudaStream_t s);
+cudaError_t mlp_grad(const float *params, const float *x, const float *t, const float *w, int64_t rows,
+                     float *const *H, float *G0, float *G1, float *f, float *g, float *grad, double *loss,
+                     cudaStream_t s);
+cudaError_t mlp_adam(float *p, const float *g, float *m, float *v, int64_t count, int64_t step, float lr,
+                     cudaStream_t s);
+cudaError_t mlp_sample(const float *x, const float *t, const float *w, int64_t rows, int batch, uint64_t seed,
+                       int64_t step, float *xb, float *tb, float *wb, cudaStream_t s);
+cudaError_t mlp_init(float *p, int *d_dims, uint64_t seed, cudaStream_t s);
+cudaError_t launch_warm_features(const double *s_col, int64_t P, int64_t n, double tau, double frac,
+                                 const double *lmax, float *u, cudaStream_t s);
+cudaError_t launch_warm_beta(const float *f, int64_t P, const double *q, double sdy, double *beta, cudaStream_t s);
+cudaError_t launch_warm_dual(const double *y, const double *xb, int64_t n, double tau, double *z, double *theta,
+                             cudaStream_t s);
 
 // Setup and reporting helpers (k_setup.cu).
 cudaError_t launch_vec_stats(const double *v, int64_t n, double *out3, cudaStream_t s);

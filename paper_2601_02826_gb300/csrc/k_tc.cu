@@ -19,12 +19,18 @@
 // active-column lists follow as in the SIMT column pass.
 //
 // Roles (256 threads): warp 0 issues TMA loads into a STAGES-deep ring,
-// warp 1 issues the MMAs (one elected thread) into a double-buffered TMEM
-// accumulator, warps 2-5 (128 threads, one per tile row) run the epilogue,
-// warps 6-7 handle the FP64 dense columns (intercept, covariates) j =
-// blockIdx.x, blockIdx.x + grid, ... <= c. CTA c takes the 128-column tiles
-// c, c + grid, c + 2 grid, ... Its active list holds its tile columns in
-// tile order, then its dense columns.
+// warp 1 issues the MMAs (one elected thread) into ACC TMEM accumulators,
+// warps 2-5 (128 threads, one per tile row) run the epilogue, warps 6-7
+// handle the FP64 dense columns (intercept, covariates) j = blockIdx.x,
+// blockIdx.x + grid, ... <= c.
+// Schedule: with R = floor(tiles / grid), CTA c takes the 128-column tiles
+// c, c + grid, ..., c + (R-1) grid whole. The rem = tiles - R grid tiles
+// left over are cut along the samples into ns slices each (ns ~ grid / rem),
+// so that the last round costs a slice instead of a tile: CTA c < rem * ns
+// computes slice c % ns of tail tile c / ns and stores its exact integer
+// digit sums; the last slice CTA of a tile to finish adds them up and runs
+// that tile's epilogue. List slot c holds CTA c's whole tiles in tile order,
+// then its dense columns; slot grid + u holds tail tile u.
 #include <cuda.h>
 #include <math.h>
 #include <stdint.h>
@@ -54,6 +60,9 @@ struct TcShape {
   static constexpr int THREADS = 256;
 };
 
+// At most this many sample slices per tail tile.
+constexpr int kMaxTailSlices = 16;
+
 __device__ __forceinline__ double dist_l1_tc(double s, double lam, double b) {
   if (b > 0.0) return fabs(s - lam);
   if (b < 0.0) return fabs(s + lam);
@@ -69,10 +78,41 @@ __device__ __forceinline__ int block_of_tc(const int64_t *__restrict__ bp, int G
   return lo;
 }
 
+// Proximal update of stored column j for every fit from V[b], the exact
+// integer value of x_j^T theta^_b in units of scale_b * 2^(-4D) (eq.
+// beta_update with M_g = eta_g I); accumulates the stop-test distance, the
+// constant term and max |a_j beta_j|, and tells whether the column is active.
+template <int NB, int D>
+__device__ __forceinline__ bool col_update(const Dsg &X, const Fits &F, int64_t j, const long long (&V)[NB],
+                                           const double *sS, const double *sScale, const int *sIdle,
+                                           const double *bcur, double *bnxt, double (&rbl)[NB],
+                                           double (&ctl)[NB], double (&wml)[NB], double aj, double bj,
+                                           double om, const double (&bo)[NB], double eta, double ie) {
+  const double dscale = ldexp(1.0, -4 * D);
+  bool act = false;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const double dot = (double)V[b] * (sScale[b] * dscale);
+    const double s = aj * dot + bj * sS[b];
+    const double lamj = F.lam[b] * om;
+    if (!sIdle[b]) {
+      rbl[b] = fmax(rbl[b], dist_l1_tc(s, lamj, bo[b]));
+      const double av = eta * bo[b] + s;
+      const double bn = (fmax(av - lamj, 0.0) - fmax(-av - lamj, 0.0)) * ie;
+      bnxt[j * NB + b] = bn;
+      ctl[b] = fma(bj, bn, ctl[b]);
+      act = act || (bn != 0.0);
+      wml[b] = fmax(wml[b], fabs(aj * bn));
+    }
+  }
+  return act;
+}
+
 template <int NB, int D>
 __global__ void __launch_bounds__(256, 1)
     k_col_tc(Dsg X, Fits F, int off, const uint8_t *__restrict__ xt, const uint8_t *__restrict__ dgt,
-             int tiles_per_cta, int *err) {
+             int rounds, int slices, int32_t *__restrict__ tail_part, unsigned *__restrict__ tail_tick,
+             int *err) {
   using Sh = TcShape<NB, D>;
   constexpr int N = Sh::N;
   constexpr int S = Sh::STAGES;
@@ -91,16 +131,21 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t base_u32 = smem_u32(smem_raw);
   uint8_t *ring = smem_raw + (((base_u32 + 1023u) & ~1023u) - base_u32);
   uint8_t *flags = ring + S * Sh::STAGE_BYTES;
-  const int T = F.T;                       // list stride: 128 * tiles_per_cta + 64
-  const int TF = 128 * tiles_per_cta;      // flags of the tile columns
+  const int T = F.T;                       // list stride: 128 * max(rounds, 1) + 64
+  const int TF = 128 * rounds;             // flags of the whole-tile columns
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = *F.it_base + off;
   const double *bcur = F.beta[k & 1];
   double *bnxt = F.beta[(k & 1) ^ 1];
   const int64_t ntiles = (X.p + 127) / 128;
-  const int ntl = (int)((blockIdx.x < ntiles) ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+  const int R = rounds, ns = slices;
+  const int rem = (int)(ntiles - (int64_t)R * gridDim.x);
+  const bool tail = rem > 0 && (int)blockIdx.x < rem * ns;
+  const int tu = tail ? (int)blockIdx.x / ns : 0, tv = tail ? (int)blockIdx.x % ns : 0;
+  const int ntl = R + (tail ? 1 : 0);      // local tile lt = R is the tail slice
   const int nk = (int)((X.n + 127) / 128);
+  const int tail_k0 = nk * tv / ns, tail_k1 = nk * (tv + 1) / ns;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -131,8 +176,9 @@ __global__ void __launch_bounds__(256, 1)
     if (lane == 0) {
       int it = 0;
       for (int lt = 0; lt < ntl; ++lt) {
-        const int tile = blockIdx.x + lt * gridDim.x;
-        for (int kc = 0; kc < nk; ++kc, ++it) {
+        const int tile = lt < R ? (int)blockIdx.x + lt * (int)gridDim.x : R * (int)gridDim.x + tu;
+        const int k0 = lt < R ? 0 : tail_k0, k1 = lt < R ? nk : tail_k1;
+        for (int kc = k0; kc < k1; ++kc, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, err, kErrEmpty)) goto producer_done;
@@ -155,8 +201,9 @@ __global__ void __launch_bounds__(256, 1)
         if (!mbar_wait(&acce[ab], aph ^ 1u, err, kErrAccEmpty)) break;
         tc_fence_after();
         const uint32_t dt = tmem + (uint32_t)(ab * N);
+        const int k0 = lt < R ? 0 : tail_k0, k1 = lt < R ? nk : tail_k1;
         bool ok = true;
-        for (int kc = 0; kc < nk; ++kc, ++it) {
+        for (int kc = k0; kc < k1; ++kc, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           if (!mbar_wait(&full[s], ph, err, kErrFull)) { ok = false; break; }
@@ -165,7 +212,7 @@ __global__ void __launch_bounds__(256, 1)
           const uint64_t ad = sdesc_k128(sa), bd = sdesc_k128(sa + Sh::A_BYTES);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            mma_f8(dt, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0 ? 1u : 0u);
+            mma_f8(dt, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc != k0 || kk != 0) ? 1u : 0u);
           mma_commit(&empty[s]);
         }
         if (!ok) break;
@@ -226,10 +273,25 @@ __global__ void __launch_bounds__(256, 1)
     // -------------------------------------------------------------- epilogue
     const int q = warp & 3;           // TMEM lane quarter of this warp
     const int m = q * 32 + lane;      // tile row = column within the tile
-    const double dscale = ldexp(1.0, -4 * D);
     for (int lt = 0; lt < ntl; ++lt) {
       const int ab = lt % kAcc;
       const uint32_t aph = (uint32_t)(lt / kAcc) & 1u;
+      if (lt >= R) {
+        // tail slice: store the exact digit sums (accumulator * 2^9) of row m
+        if (!mbar_wait(&accf[ab], aph, err, kErrAccFull)) break;
+        tc_fence_after();
+        uint32_t r[N];
+#pragma unroll
+        for (int c = 0; c < N / 16; ++c)
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * N + 16 * c), r + 16 * c);
+        tmem_wait_ld();
+        tc_fence_before();
+        mbar_arrive(&acce[ab]);
+        int32_t *dst = tail_part + (int64_t)(tu * ns + tv) * Sh::NR * 128 + m;
+#pragma unroll
+        for (int d = 0; d < Sh::NR; ++d) dst[d * 128] = __float2int_rn(__uint_as_float(r[d]) * 512.0f);
+        continue;
+      }
       // operands of this thread's column, fetched while the MMAs run
       const int tile = blockIdx.x + lt * gridDim.x;
       const int64_t sidx = (int64_t)tile * 128 + m;
@@ -252,31 +314,19 @@ __global__ void __launch_bounds__(256, 1)
       tc_fence_before();
       mbar_arrive(&acce[ab]);
       if (!live) continue;
-      bool act = false;
+      // exact recombination of the digit sums: value = 2^9 * accumulator
+      long long V[NB];
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        // exact recombination of the digit sums: value = 2^9 * accumulator
-        long long V = 0;
+        V[b] = 0;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
           const float f = __uint_as_float(r[b * D + d]) * 512.0f;
-          V = V * 16 + (long long)__float2int_rn(f);
-        }
-        const double dot = (double)V * (sScale[b] * dscale);
-        const double s = aj * dot + bj * sS[b];
-        const double lamj = F.lam[b] * om;
-        if (!sIdle[b]) {
-          rbl[b] = fmax(rbl[b], dist_l1_tc(s, lamj, bo[b]));
-          // eq. beta_update with M_g = eta_g I
-          const double av = eta * bo[b] + s;
-          const double bn = (fmax(av - lamj, 0.0) - fmax(-av - lamj, 0.0)) * ie;
-          bnxt[j * NB + b] = bn;
-          ctl[b] = fma(bj, bn, ctl[b]);
-          act = act || (bn != 0.0);
-          wml[b] = fmax(wml[b], fabs(aj * bn));
+          V[b] = V[b] * 16 + (long long)__float2int_rn(f);
         }
       }
-      if (act) flags[lt * 128 + m] = 1;
+      if (col_update<NB, D>(X, F, j, V, sS, sScale, sIdle, bcur, bnxt, rbl, ctl, wml, aj, bj, om, bo, eta, ie))
+        flags[lt * 128 + m] = 1;
     }
   }
   __syncthreads();
@@ -323,6 +373,89 @@ __global__ void __launch_bounds__(256, 1)
     int tot = scan[Sh::THREADS - 1];
     for (int d = 0; d < s_ndense; ++d) lst[tot++] = s_dense_act[d];
     F.a_cnt[blockIdx.x] = tot;
+  }
+  if (tail) {
+    // the last slice CTA of tail tile tu to finish runs its epilogue into
+    // list slot grid + tu (one thread per column)
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(tail_tick + tu, 1u) == (unsigned)(ns - 1)) ? 1 : 0;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      const int slot = (int)gridDim.x + tu;
+      const int m = threadIdx.x;
+      const int64_t sidx = (int64_t)(R * (int)gridDim.x + tu) * 128 + m;
+      const bool live = m < 128 && sidx < X.p;
+      // sums over the slices of the digit sums, 4 columns per int4, every
+      // slice's load in flight at once, into the (idle) stage ring
+      int32_t *tsum = reinterpret_cast<int32_t *>(ring);
+      for (int q = threadIdx.x; q < Sh::NR * 32; q += Sh::THREADS) {
+        int4 v4[kMaxTailSlices];
+#pragma unroll
+        for (int v = 0; v < kMaxTailSlices; ++v)
+          if (v < ns)
+            v4[v] = __ldcg(reinterpret_cast<const int4 *>(tail_part + (int64_t)(tu * ns + v) * Sh::NR * 128) + q);
+        int4 a = make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int v = 0; v < kMaxTailSlices; ++v)
+          if (v < ns) { a.x += v4[v].x; a.y += v4[v].y; a.z += v4[v].z; a.w += v4[v].w; }
+        reinterpret_cast<int4 *>(tsum)[q] = a;
+      }
+      __syncthreads();
+      double rb2[NB], ct2[NB], wm2[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) { rb2[b] = 0.0; ct2[b] = 0.0; wm2[b] = 0.0; }
+      bool act = false;
+      int64_t j = 0;
+      if (live) {
+        j = 1 + X.c + sidx;
+        long long V[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          V[b] = 0;
+#pragma unroll
+          for (int d = 0; d < D; ++d) V[b] = V[b] * 16 + (long long)tsum[(b * D + d) * 128 + m];
+        }
+        const double aj = __ldg(X.a + j), bj = __ldg(X.b + j), om = __ldg(F.omega + j);
+        double bo[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) bo[b] = bcur[j * NB + b];
+        const int g = block_of_tc(F.block_ptr, F.G, j);
+        const double eta = __ldg(F.eta + g), ie = __ldg(F.inv_eta + g);
+        act = col_update<NB, D>(X, F, j, V, sS, sScale, sIdle, bcur, bnxt, rb2, ct2, wm2, aj, bj, om, bo, eta,
+                                ie);
+      }
+      for (int b = 0; b < NB; ++b) {
+        red[0][threadIdx.x] = rb2[b];
+        red[1][threadIdx.x] = ct2[b];
+        red[2][threadIdx.x] = wm2[b];
+        __syncthreads();
+        const int ops[3] = {0, 1, 0};
+        tree_reduce<3>(red, ops, 256);
+        if (threadIdx.x == 0) {
+          F.a_rb[slot * NB + b] = red[0][0];
+          F.a_ct[slot * NB + b] = red[1][0];
+          F.a_wmax[slot * NB + b] = red[2][0];
+        }
+        __syncthreads();
+      }
+      // ordered compaction of the tile's active columns
+      scan[threadIdx.x] = act ? 1 : 0;
+      __syncthreads();
+      for (int o = 1; o < Sh::THREADS; o <<= 1) {
+        int v = (threadIdx.x >= (unsigned)o) ? scan[threadIdx.x - o] : 0;
+        __syncthreads();
+        scan[threadIdx.x] += v;
+        __syncthreads();
+      }
+      if (act) F.a_list[(int64_t)slot * T + scan[threadIdx.x] - 1] = (int)j;
+      if (threadIdx.x == Sh::THREADS - 1) {
+        F.a_cnt[slot] = scan[Sh::THREADS - 1];
+        tail_tick[tu] = 0u;
+      }
+    }
   }
   col_finalize<NB>(F);
 }
@@ -410,12 +543,15 @@ __global__ void k_tile_x(Dsg X, uint8_t *xt, int64_t nk) {
 //                the digit bytes, written as the byte image of one K-major
 //                swizzled operand tile per block of 128 active positions;
 //   k_xbeta_tc   CTA (rt, sp): samples [128 rt, +128) (M, the TMEM lanes)
-//                over the blocks of split sp. One thread streams a ring of
-//                stages: TMA tile::gather4 brings the 128-byte sample runs of
-//                4 active columns at a time into an MN-major operand, a bulk
-//                copy brings the block's digit tile, and kind::f8f6f4 MMAs
-//                accumulate exact integer sums in FP32 in TMEM. The epilogue
-//                writes one exact int64 partial per (split, sample, fit).
+//                over the blocks of split sp. Its threads load the 128-byte
+//                sample runs of a block's active columns with 16-byte loads
+//                (one block ahead) into a 2-stage ring as an MN-major
+//                operand, a bulk copy brings the block's digit tile, and
+//                kind::f8f6f4 MMAs accumulate exact integer sums in FP32 in
+//                TMEM. The epilogue writes one exact int64 partial per
+//                (split, sample, fit). (TMA tile::gather4 of the runs, 4
+//                columns per copy, ran at about 1.5 TB/s here: the copies,
+//                not HBM, set the pace.)
 template <int NB, int DWD>
 struct XbShape {
   static constexpr int NR = NB * DWD;
@@ -423,7 +559,7 @@ struct XbShape {
   static constexpr int A_BYTES = 128 * 128;
   static constexpr int B_BYTES = N * 128;
   static constexpr int BUF = A_BYTES + B_BYTES;
-  static constexpr int STAGES = 4;
+  static constexpr int STAGES = 2;
   static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
 };
 
@@ -502,15 +638,19 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-// CTA (rt, sp). With fuse = 1 the last split CTA to finish a row tile sums
+// CTA (rt, sp). All 128 threads stream the blocks of split sp: each thread
+// loads 8 16-byte sample runs of the block's active columns (column k =
+// chunk / 8, samples 16 (chunk % 8) .. +15 of the row tile; the indices one
+// block ahead) and stores them into the stage as the 128-byte-swizzled
+// MN-major operand; thread 0 adds the block's digit tile by a bulk copy and
+// issues the MMAs. With fuse = 1 the last split CTA to finish a row tile sums
 // the splits' integer partials of its 128 rows and applies the vector update
 // (z, r, theta and the stop-test partials, as k_vec), and the last row tile
-// to finish writes the totals; the operands of that update that do not
-// depend on this pass are loaded before the pipeline drains.
+// to finish writes the totals.
 template <int NB, int DWD>
 __global__ void __launch_bounds__(128)
     k_xbeta_tc(Dsg X, Fits F, int off, int fuse, const int *__restrict__ scol, const uint8_t *__restrict__ wtile,
-               const __grid_constant__ CUtensorMap tmX, int *err) {
+               int *err) {
   using Sh = XbShape<NB, DWD>;
   constexpr int N = Sh::N;
   constexpr int ST = Sh::STAGES;
@@ -533,7 +673,121 @@ __global__ void __launch_bounds__(128)
   const bool row = i < F.n;
   long long *out = F.xb_ipart + (int64_t)blockIdx.y * F.npad * NB;
 
-  // operands of the fused vector update (independent of this pass)
+  long long V[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) V[b] = 0;
+  if (has) {
+    if (tid == 0) {
+      for (int q = 0; q < ST; ++q) { mbar_init(&full[q], 128); mbar_init(&empty[q], 1); }
+      mbar_init(&dbar, 1);
+      fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, Sh::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = idesc_f32acc_amn(0u, 128u, (uint32_t)N);
+    // this thread's sample chunk c and the columns k = 16 e + kr (e < 8)
+    const int c = tid & 7, kr = tid >> 3;
+    const int64_t s0 = i0 + 16 * c;                 // first sample of the chunk
+    const bool cin = s0 < F.n;                      // chunk inside the samples
+    const int valid = cin ? (int)(F.n - s0 < 16 ? F.n - s0 : 16) : 0;
+    const int nb = kb1 - kb0;
+    int idx[8];
+    int4 cur[8];
+    auto load_idx = [&](int blk) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) idx[e] = __ldg(scol + (int64_t)blk * 128 + 16 * e + kr);
+    };
+    auto load_data = [&](int4 (&v)[8]) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        v[e] = make_int4(0, 0, 0, 0);
+        if (cin && idx[e] < X.p)
+          v[e] = __ldg(reinterpret_cast<const int4 *>(X.geno + (int64_t)idx[e] * X.ld + s0));
+      }
+    };
+    load_idx(kb0);
+    load_data(cur);
+    if (nb > 1) load_idx(kb0 + 1);
+    bool ok = true;
+    for (int it = 0; it < nb && ok; ++it) {
+      const int s = it % ST;
+      const uint32_t ph = (uint32_t)(it / ST) & 1u;
+      int4 nxt[8];
+      if (it + 1 < nb) {
+        load_data(nxt);
+        if (it + 2 < nb) load_idx(kb0 + it + 2);
+      }
+      if (!mbar_wait(&empty[s], ph ^ 1u, err, kErrEmpty)) { ok = false; break; }
+      uint8_t *stage = ring + s * Sh::BUF;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        int4 v = cur[e];
+        if (valid < 16) {  // bytes of samples >= n are zero
+          uint32_t w[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int keep = min(max(valid - 4 * q, 0), 4);
+            w[q] &= (keep >= 4) ? 0xFFFFFFFFu : ((1u << (8 * keep)) - 1u);
+          }
+          v = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+        }
+        const int kk = 16 * e + kr;
+        *reinterpret_cast<int4 *>(stage + kk * 128 + ((c ^ (kk & 7)) << 4)) = v;
+      }
+      fence_proxy_async();
+      if (tid == 0) {
+        mbar_arrive_expect_tx(&full[s], Sh::B_BYTES);
+        bulk_load(stage + Sh::A_BYTES, wtile + (int64_t)(kb0 + it) * Sh::B_BYTES, Sh::B_BYTES, &full[s]);
+        if (!mbar_wait(&full[s], ph, err, kErrFull)) {
+          ok = false;
+        } else {
+          tc_fence_after();
+          const uint32_t sa = smem_u32(stage);
+          const uint64_t ad = sdesc_mn128(sa), bd = sdesc_k128(sa + Sh::A_BYTES);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            mma_f8(tmem, ad + (uint64_t)(q * 256), bd + (uint64_t)(q * 2), idesc, (it | q) != 0 ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+      } else {
+        mbar_arrive(&full[s]);
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) cur[e] = nxt[e];
+    }
+    if (tid == 0) mma_commit(&dbar);
+    __syncwarp();
+    const bool done = mbar_wait(&dbar, 0u, err, kErrAccFull) && ok;
+    tc_fence_after();
+    // TMEM lane = sample row, columns b*DWD + d
+    uint32_t r[N];
+#pragma unroll
+    for (int cc = 0; cc < N / 16; ++cc)
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * cc), r + 16 * cc);
+    tmem_wait_ld();
+    if (done)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        long long v = 0;
+#pragma unroll
+        for (int d = 0; d < DWD; ++d) {
+          const float f = __uint_as_float(r[b * DWD + d]) * 512.0f;
+          v = v * 16 + (long long)__float2int_rn(f);
+        }
+        V[b] = v;
+      }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tc_fence_after();
+      tmem_dealloc(tmem, Sh::TMEM_COLS);
+    }
+  }
+
+  // operands of the fused vector update
   const int k = fuse ? (*F.it_base + off) : 0;
   bool run[NB];
   double yi = 0.0, zo[NB], th[NB], ro[NB], cv[NB];
@@ -557,95 +811,6 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int b = 0; b < NB; ++b) cv[b] = fma(aj * __ldg(bt + j * NB + b), x, cv[b]);
       }
-    }
-  }
-
-  long long V[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) V[b] = 0;
-  if (has) {
-    if (tid == 0) {
-      for (int q = 0; q < ST; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
-      mbar_init(&dbar, 1);
-      fence_mbar_init();
-    }
-    if (warp == 0) tmem_alloc(&tmem_base, Sh::TMEM_COLS);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_base;
-    if (warp == 0) {
-      // warp 0 streams the blocks: lane l gathers active columns 4l..4l+3 of
-      // a block (its column indices loaded one block ahead); lane 0 also
-      // loads the digit tile and issues the MMAs
-      const int lane = tid & 31;
-      const uint32_t idesc = idesc_f32acc_amn(0u, 128u, (uint32_t)N);
-      const int nb = kb1 - kb0;
-      bool ok = true;
-      int4 c4n = __ldg(reinterpret_cast<const int4 *>(scol + (int64_t)kb0 * 128) + lane);
-      for (int it = 0; it < nb + ST; ++it) {
-        if (it < nb) {
-          const int4 c4 = c4n;
-          if (it + 1 < nb) c4n = __ldg(reinterpret_cast<const int4 *>(scol + (int64_t)(kb0 + it + 1) * 128) + lane);
-          const int s = it % ST;
-          const uint32_t ph = (uint32_t)(it / ST) & 1u;
-          int okl = 1;
-          if (lane == 0) {
-            okl = mbar_wait(&empty[s], ph ^ 1u, err, kErrEmpty) ? 1 : 0;
-            if (okl) {
-              mbar_arrive_expect_tx(&full[s], Sh::BUF);
-              bulk_load(ring + s * Sh::BUF + Sh::A_BYTES, wtile + (int64_t)(kb0 + it) * Sh::B_BYTES, Sh::B_BYTES,
-                        &full[s]);
-            }
-          }
-          okl = __shfl_sync(0xffffffffu, okl, 0);
-          if (!okl) { ok = false; break; }
-          tma_gather4(ring + s * Sh::BUF + lane * 512, &tmX, &full[s], (int)i0, c4.x, c4.y, c4.z, c4.w);
-        }
-        const int mt = it - (ST - 1);
-        if (lane == 0 && mt >= 0 && mt < nb) {
-          const int s = mt % ST;
-          const uint32_t ph = (uint32_t)(mt / ST) & 1u;
-          if (!mbar_wait(&full[s], ph, err, kErrFull)) {
-            ok = false;
-          } else {
-            tc_fence_after();
-            const uint32_t sa = smem_u32(ring + s * Sh::BUF);
-            const uint64_t ad = sdesc_mn128(sa), bd = sdesc_k128(sa + Sh::A_BYTES);
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              mma_f8(tmem, ad + (uint64_t)(kk * 256), bd + (uint64_t)(kk * 2), idesc, (mt | kk) != 0 ? 1u : 0u);
-            mma_commit(&empty[s]);
-          }
-        }
-        if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
-      }
-      if (lane == 0) mma_commit(&dbar);
-    }
-    __syncwarp();
-    const bool done = mbar_wait(&dbar, 0u, err, kErrAccFull);
-    tc_fence_after();
-    // TMEM lane = sample row, columns b*DWD + d
-    uint32_t r[N];
-#pragma unroll
-    for (int c = 0; c < N / 16; ++c) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * c), r + 16 * c);
-    tmem_wait_ld();
-    if (done)
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        long long v = 0;
-#pragma unroll
-        for (int d = 0; d < DWD; ++d) {
-          const float f = __uint_as_float(r[b * DWD + d]) * 512.0f;
-          v = v * 16 + (long long)__float2int_rn(f);
-        }
-        V[b] = v;
-      }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-      tc_fence_after();
-      tmem_dealloc(tmem, Sh::TMEM_COLS);
     }
   }
   if (!fuse || S > 1) {
@@ -717,17 +882,16 @@ __global__ void __launch_bounds__(128)
 }
 
 template <int NB, int DWD>
-size_t g_xt_opted = 48 * 1024;
+size_t g_xt_opted = 0;  // the attribute is set on first use (static + dynamic may pass 48 KB)
 
 size_t xbeta_tc_smem(int NB, int DWD) {
   const int N = ((NB * DWD + 15) / 16) * 16;
-  return (size_t)4 * (128 * 128 + N * 128) + 1024 + 16;
+  return (size_t)2 * (128 * 128 + N * 128) + 1024 + 16;
 }
 
 template <int NB, int DWD>
 static cudaError_t xbeta_tc_t(const Dsg &X, const Fits &F, int off, int fuse, const double *beta_in,
-                              const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err, int num_sms,
-                              cudaStream_t s) {
+                              int *scol, uint8_t *wtile, int *err, int num_sms, cudaStream_t s) {
   const size_t smem = xbeta_tc_smem(NB, DWD);
   if (smem > g_xt_opted<NB, DWD>) {
     cudaError_t e = cudaFuncSetAttribute(k_xbeta_tc<NB, DWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -750,19 +914,19 @@ static cudaError_t xbeta_tc_t(const Dsg &X, const Fits &F, int off, int fuse, co
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)rows, kXTMaxSplits);
-  k_xbeta_tc<NB, DWD><<<grid, 128, smem, s>>>(X, F, off, fuse, scol, wtile, tmX, err);
+  k_xbeta_tc<NB, DWD><<<grid, 128, smem, s>>>(X, F, off, fuse, scol, wtile, err);
   return cudaGetLastError();
 }
 
 // scol: (P + 127)/128*128 ints; wtile: (P + 127)/128 tiles of N*128 bytes.
 cudaError_t launch_xbeta_tc(int NB, const Dsg &X, const Fits &F, int off, int fuse, const double *beta_in,
-                            const CUtensorMap &tmX, int *scol, uint8_t *wtile, int *err, int num_sms,
-                            cudaStream_t s) {
+                            int *scol, uint8_t *wtile, int *err, int num_sms, cudaStream_t s) {
   switch (NB) {
-    case 1: return xbeta_tc_t<1, 11>(X, F, off, fuse, beta_in, tmX, scol, wtile, err, num_sms, s);
-    case 2: return xbeta_tc_t<2, 11>(X, F, off, fuse, beta_in, tmX, scol, wtile, err, num_sms, s);
-    case 3: return xbeta_tc_t<3, 11>(X, F, off, fuse, beta_in, tmX, scol, wtile, err, num_sms, s);
-    case 4: return xbeta_tc_t<4, 11>(X, F, off, fuse, beta_in, tmX, scol, wtile, err, num_sms, s);
+    case 1: return xbeta_tc_t<1, 11>(X, F, off, fuse, beta_in, scol, wtile, err, num_sms, s);
+    case 2: return xbeta_tc_t<2, 11>(X, F, off, fuse, beta_in, scol, wtile, err, num_sms, s);
+    case 3: return xbeta_tc_t<3, 11>(X, F, off, fuse, beta_in, scol, wtile, err, num_sms, s);
+    case 4: return xbeta_tc_t<4, 11>(X, F, off, fuse, beta_in, scol, wtile, err, num_sms, s);
+    case 8: return xbeta_tc_t<8, 11>(X, F, off, fuse, beta_in, scol, wtile, err, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -772,34 +936,50 @@ int xbeta_tc_rows(int NB) { return ((NB * 11 + 15) / 16) * 16; }
 // ------------------------------------------------------------------ host
 
 template <int NB, int D>
-size_t g_tc_opted = 48 * 1024;
+size_t g_tc_opted = 0;  // the attribute is set on first use
 
 size_t col_tc_smem(int NB, int D, int T) {
   int N = NB * D <= 16 ? 16 : (NB * D <= 32 ? 32 : 64);
   return (size_t)6 * (128 * 128 + N * 128) + 1024 + (size_t)T + 16;  // flags use <= T bytes
 }
 
+void col_tc_schedule(int64_t p, int64_t n, int num_sms, TcSchedule *out) {
+  const int64_t tiles = (p + 127) / 128, nk = (n + 127) / 128;
+  TcSchedule &sc = *out;
+  sc.grid = std::max(1, num_sms);  // one CTA per SM, even with fewer tiles (they are then sliced)
+  sc.rounds = (int)(tiles / sc.grid);
+  sc.rem = (int)(tiles - (int64_t)sc.rounds * sc.grid);
+  sc.slices = sc.rem ? (int)std::max<int64_t>(
+                            1, std::min<int64_t>(std::min<int64_t>(nk, sc.grid / sc.rem), kMaxTailSlices))
+                     : 0;
+  sc.list_stride = 128 * std::max(sc.rounds, 1) + 64;
+  sc.slots = sc.grid + sc.rem;
+}
+
+int tc_tail_rows(int NB, int D) { return NB * D; }
+
 template <int NB, int D>
 static cudaError_t col_tc_t(const Dsg &X, const Fits &F, int off, const uint8_t *xt,
-                            const uint8_t *dgt, int grid, int tiles_per_cta, int *err,
-                            cudaStream_t s) {
+                            const uint8_t *dgt, const TcSchedule &sc, int32_t *tail_part,
+                            unsigned *tail_tick, int *err, cudaStream_t s) {
   const size_t smem = col_tc_smem(NB, D, F.T);
   if (smem > g_tc_opted<NB, D>) {
     cudaError_t e = cudaFuncSetAttribute(k_col_tc<NB, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     g_tc_opted<NB, D> = smem;
   }
-  k_col_tc<NB, D><<<grid, TcShape<NB, D>::THREADS, smem, s>>>(X, F, off, xt, dgt, tiles_per_cta, err);
+  k_col_tc<NB, D><<<sc.grid, TcShape<NB, D>::THREADS, smem, s>>>(X, F, off, xt, dgt, sc.rounds, sc.slices,
+                                                                   tail_part, tail_tick, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, const uint8_t *xt,
-                          const uint8_t *dgt, int grid, int tiles_per_cta, int *err,
-                          cudaStream_t s) {
+                          const uint8_t *dgt, const TcSchedule &sc, int32_t *tail_part,
+                          unsigned *tail_tick, int *err, cudaStream_t s) {
 #define FSQR_TC_CASE(nb, d) \
-  if (NB == nb && D == d) return col_tc_t<nb, d>(X, F, off, xt, dgt, grid, tiles_per_cta, err, s);
-  FSQR_TC_CASE(1, 7) FSQR_TC_CASE(2, 7) FSQR_TC_CASE(3, 7) FSQR_TC_CASE(4, 7)
-  FSQR_TC_CASE(1, 6) FSQR_TC_CASE(2, 6) FSQR_TC_CASE(3, 6) FSQR_TC_CASE(4, 6)
+  if (NB == nb && D == d) return col_tc_t<nb, d>(X, F, off, xt, dgt, sc, tail_part, tail_tick, err, s);
+  FSQR_TC_CASE(1, 7) FSQR_TC_CASE(2, 7) FSQR_TC_CASE(3, 7) FSQR_TC_CASE(4, 7) FSQR_TC_CASE(8, 7)
+  FSQR_TC_CASE(1, 6) FSQR_TC_CASE(2, 6) FSQR_TC_CASE(3, 6) FSQR_TC_CASE(4, 6) FSQR_TC_CASE(8, 6)
 #undef FSQR_TC_CASE
   return cudaErrorInvalidValue;
 }
@@ -809,8 +989,8 @@ cudaError_t launch_quantize_tc(int NB, int D, const Fits &F, int off, uint8_t *d
   const unsigned grid = (unsigned)((total + 255) / 256);
 #define FSQR_Q_CASE(nb, d) \
   if (NB == nb && D == d) { k_quantize_tc<nb, d><<<grid, 256, 0, s>>>(F, off, dg); return cudaGetLastError(); }
-  FSQR_Q_CASE(1, 7) FSQR_Q_CASE(2, 7) FSQR_Q_CASE(3, 7) FSQR_Q_CASE(4, 7)
-  FSQR_Q_CASE(1, 6) FSQR_Q_CASE(2, 6) FSQR_Q_CASE(3, 6) FSQR_Q_CASE(4, 6)
+  FSQR_Q_CASE(1, 7) FSQR_Q_CASE(2, 7) FSQR_Q_CASE(3, 7) FSQR_Q_CASE(4, 7) FSQR_Q_CASE(8, 7)
+  FSQR_Q_CASE(1, 6) FSQR_Q_CASE(2, 6) FSQR_Q_CASE(3, 6) FSQR_Q_CASE(4, 6) FSQR_Q_CASE(8, 6)
 #undef FSQR_Q_CASE
   return cudaErrorInvalidValue;
 }

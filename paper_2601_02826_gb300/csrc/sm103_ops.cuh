@@ -1,5 +1,5 @@
-// Inline-PTX building blocks for sm_103a: mbarriers with bounded waits, TMA
-// tile loads, and the 5th-generation tensor core (tcgen05) with its tensor
+// Inline-PTX building blocks for sm_103a: mbarriers with bounded waits, bulk
+// (TMA) copies, and the 5th-generation tensor core (tcgen05) with its tensor
 // memory (TMEM). Every wait gives up after a cycle budget and records an
 // error code instead of spinning forever.
 #pragma once
@@ -67,24 +67,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
   }
 }
 
-// 2-D TMA tile load into shared memory, completing on an mbarrier.
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
 // 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16),
 // completing on an mbarrier.
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
-}
-
-__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
-  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
 // ---- tensor memory ----------------------------------------------------------
@@ -183,18 +171,6 @@ __device__ __forceinline__ bool elect_one() {
 
 namespace fsqr {
 namespace sm103 {
-
-// TMA gather of 4 rows (y0..y3) of a 2-D tensor, each box0 elements wide from
-// column x, into 4 consecutive box rows in shared memory (box one row high).
-__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y0,
-                                            int y1, int y2, int y3) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-      "%4, %5, %6}], [%7];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3),
-        "r"(smem_u32(bar))
-      : "memory");
-}
 
 // Shared-memory descriptor of an MN-major operand with the 128-byte swizzle:
 // 128-byte rows hold 128 consecutive M elements (8-bit) of one k; 8 rows form

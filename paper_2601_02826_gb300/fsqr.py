@@ -63,7 +63,8 @@ EXPORTS = ["fsqr_version", "fsqr_opts_default", "fsqr_create", "fsqr_destroy", "
            "fsqr_col_stats", "fsqr_lambda_max", "fsqr_eta", "fsqr_fit", "fsqr_fit_batch",
            "fsqr_fit_batch_host", "fsqr_kkt", "fsqr_predict", "fsqr_back_transform",
            "fsqr_profile_enable", "fsqr_profile_get", "fsqr_profile_reset",
-           "fsqr_lambda_max_noalloc"]
+           "fsqr_lambda_max_noalloc", "fsqr_mlp_param_count", "fsqr_mlp_init", "fsqr_mlp_forward",
+           "fsqr_mlp_grad", "fsqr_mlp_train", "fsqr_warm_features", "fsqr_warm_start"]
 
 _lib = None
 
@@ -104,9 +105,18 @@ def load(path: str | None = None):
     L.fsqr_profile_enable.argtypes = [vp, i32]
     L.fsqr_profile_get.argtypes = [vp, C.POINTER(Profile)]
     L.fsqr_profile_reset.argtypes = [vp]
+    u64, flt = C.c_uint64, C.c_float
+    L.fsqr_mlp_param_count.argtypes = []
+    L.fsqr_mlp_init.argtypes = [vp, vp, u64]
+    L.fsqr_mlp_forward.argtypes = [vp, vp, vp, i64, vp]
+    L.fsqr_mlp_grad.argtypes = [vp, vp, vp, vp, vp, i64, vp, pd]
+    L.fsqr_mlp_train.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, i64, i32, i32, flt, u64, pd]
+    L.fsqr_warm_features.argtypes = [vp, pD, vp, dbl, dbl, vp, vp, pd]
+    L.fsqr_warm_start.argtypes = [vp, pD, vp, dbl, dbl, vp, vp, vp, vp, vp]
     for f in EXPORTS:
         if f not in ("fsqr_opts_default", "fsqr_last_error", "fsqr_version"):
             getattr(L, f).restype = i32
+    L.fsqr_mlp_param_count.restype = i64
     _lib = L
     return L
 
@@ -258,6 +268,40 @@ class Context:
         self._check(self.L.fsqr_kkt(self.h, C.byref(d), _ptr(y), tau, lam, _ptr(omega), lam_norm,
                                     _ptr(beta), _ptr(z), _ptr(theta), C.byref(info)))
         return info
+
+    # ---- learned warm start (float32 device tensors for the network)
+
+    def mlp_param_count(self) -> int:
+        return int(self.L.fsqr_mlp_param_count())
+
+    def mlp_init(self, params, seed: int):
+        self._check(self.L.fsqr_mlp_init(self.h, _ptr(params), seed))
+
+    def mlp_forward(self, params, x, out):
+        self._check(self.L.fsqr_mlp_forward(self.h, _ptr(params), _ptr(x), x.shape[0], _ptr(out)))
+
+    def mlp_grad(self, params, x, t, w, grad) -> float:
+        loss = C.c_double()
+        self._check(self.L.fsqr_mlp_grad(self.h, _ptr(params), _ptr(x), _ptr(t), _ptr(w), x.shape[0],
+                                         _ptr(grad), C.byref(loss)))
+        return loss.value
+
+    def mlp_train(self, params, m, v, step0, x, t, w, steps, batch, lr, seed) -> np.ndarray:
+        losses = np.zeros(max(steps, 1))
+        self._check(self.L.fsqr_mlp_train(self.h, _ptr(params), _ptr(m), _ptr(v), step0, _ptr(x), _ptr(t),
+                                          _ptr(w), x.shape[0], steps, batch, lr, seed,
+                                          losses.ctypes.data_as(C.POINTER(C.c_double))))
+        return losses[:steps]
+
+    def warm_features(self, d, y, tau, lam_frac, omega, u) -> float:
+        lmax = C.c_double()
+        self._check(self.L.fsqr_warm_features(self.h, C.byref(d), _ptr(y), tau, lam_frac, _ptr(omega), _ptr(u),
+                                              C.byref(lmax)))
+        return lmax.value
+
+    def warm_start(self, d, y, tau, lam_frac, omega, params, beta, z, theta):
+        self._check(self.L.fsqr_warm_start(self.h, C.byref(d), _ptr(y), tau, lam_frac, _ptr(omega),
+                                           _ptr(params), _ptr(beta), _ptr(z), _ptr(theta)))
 
     def predict(self, d, beta, B, out):
         self._check(self.L.fsqr_predict(self.h, C.byref(d), _ptr(beta), B, _ptr(out)))

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "fsqr.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(?:int|void|const char \*)\s*\*?\s*(fsqr_\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(?:int64_t|int|void|const char \*)\s*\*?\s*(fsqr_\w+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():

@@ -177,6 +177,46 @@ def test_mixed_iterates_track_fp64(ctx, case, precision, digits):
     assert max_rel(t, ref.theta) <= 1e-7
 
 
+def test_mixed_iterates_track_fp64_sliced_tail(ctx):
+    """More 128-column tiles (192) than SMs: each CTA takes a whole tile and the
+    40 left over are cut into sample slices whose integer digit sums are added
+    up by the last slice to finish (3 slices of 8 sample blocks: 2, 3, 3)."""
+    w = synth.tiny_geno(113, 1000, 24576, c=2, fmt=synth.FMT_INT8, G=7, taus=(0.4,))
+    tau = w.taus[0]
+    d, lmax, lam_s, lam, mu, bp, eta = oracle_problem(w, tau, 0.2)
+    dw = _up(ctx, w)
+    _, _, b, z, t = _run(ctx, dw, w, tau, lam_s, mu, eta, 30, precision=1, digits=4)
+    ref = O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=0.0, max_iter=30)
+    assert max_rel(b, ref.beta) <= 1e-7
+    assert max_rel(t, ref.theta) <= 1e-7
+    assert max_rel(z, ref.z) <= 1e-7
+
+
+def test_batch_of_eight_fits_on_tensor_cores(ctx):
+    """8 fits (4 tau x 2 lambda) advanced together per X pass on the tensor
+    cores: 56 digit rows of theta, 88 of the X~ beta weights."""
+    w = synth.tiny_geno(106, 260, 700, c=2, fmt=synth.FMT_INT8, G=3, taus=(0.3,))
+    dw = _up(ctx, w)
+    d = O.build_design(O.decode_stored(w.geno, w.fmt, w.n), w.cov)
+    taus = [0.15, 0.4, 0.6, 0.85]
+    fr = [0.5, 0.25]
+    lmaxs = [O.lambda_max(d.Xt, w.y, t, w.omega) for t in taus]
+    lams = np.array([[f * lm for f in fr] for lm in lmaxs])
+    B = 8
+    beta = torch.zeros(B * w.P, dtype=torch.float64, device="cuda")
+    z = torch.zeros(B * w.n, dtype=torch.float64, device="cuda")
+    th = torch.zeros(B * w.n, dtype=torch.float64, device="cuda")
+    rc, infos = ctx.fit_batch(dw.design, dw.y, taus, lams, dw.omega, w.block_ptr(), beta, z, th,
+                              opts=dict(tol=1e-6, max_iter=1_000_000, precision=1, max_group=8))
+    assert rc == 0
+    bb, zz, tt = to_np(beta).reshape(B, -1), to_np(z).reshape(B, -1), to_np(th).reshape(B, -1)
+    for t_i, tau in enumerate(taus):
+        for l_i in range(len(fr)):
+            f = t_i * len(fr) + l_i
+            lam = lams[t_i, l_i] * w.omega
+            assert O.kkt(d.Xt, w.y, tau, lam, lmaxs[t_i], bb[f], zz[f], tt[f]).value <= 1.001e-6, f
+
+
 def test_batch_grid_and_path_warm_start(ctx):
     w = synth.tiny_geno(105, 300, 400, c=1, fmt=synth.FMT_INT8, G=3, taus=(0.25, 0.75))
     dw = _up(ctx, w)
