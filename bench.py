@@ -374,6 +374,61 @@ def run_reference(args, rank, world):
     print(json.dumps(out))
 
 
+def run_grid_sample(args, local_rank):
+    """Batched-grid sample (not the contract line): the 10,000 x 500,000 int8
+    workload of the tau x lambda grid, one group of 8 fits (tau = 0.1..0.8
+    at 0.1 lambda_max) advanced together on the tensor cores for a fixed
+    number of iterations. Reports the time per iteration, the fit-iterations
+    per second and the column pass against the HBM roofline."""
+    import torch
+
+    from paper_2601_02826_gb300 import fsqr, synth
+    from paper_2601_02826_gb300.device import upload
+
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fsqr.Context(local_rank, stream.cuda_stream)
+    t0 = time.perf_counter()
+    w = synth.grid_int8()
+    t_gen = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        dw = upload(ctx, w, device=dev)
+    stream.synchronize()
+    taus = w.taus[:8]
+    B = len(taus)
+    lam = [LAMBDA_FRAC * ctx.lambda_max(dw.design, dw.y, t, dw.omega) for t in taus]
+    beta = torch.zeros(B * w.P, dtype=torch.float64, device=dev)
+    z = torch.zeros(B * w.n, dtype=torch.float64, device=dev)
+    th = torch.zeros(B * w.n, dtype=torch.float64, device=dev)
+    iters = args.profile_iters or 400
+    opts = dict(tol=0.0, max_iter=iters, precision=fsqr.MIXED, digits=4, max_group=8)
+    ctx.fit_batch(dw.design, dw.y, taus, lam, dw.omega, w.block_ptr(), beta, z, th,
+                  opts=dict(opts, max_iter=20))
+    ctx.profile(enable=True, reset=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, infos = ctx.fit_batch(dw.design, dw.y, taus, lam, dw.omega, w.block_ptr(), beta, z, th, opts=opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile(enable=False)
+    col_ms = prof.col_ms / max(1, prof.col_samples)
+    peak, kind = measured_peaks()
+    gbs = prof.col_bytes / (col_ms / 1e3) / 1e9
+    out = {"sample": "batched grid, one group of 8 fits, fixed iterations (setup included)",
+           "workload": "grid_int8", "n": w.n, "p": w.p, "G": len(w.block_sizes), "fits": B,
+           "iterations": iters, "ms": ms, "ms_per_iteration": ms / iters,
+           "fit_iterations_per_s": B * iters / (ms / 1e3),
+           "col": {"avg_launch_ms": col_ms, "bytes_per_launch": prof.col_bytes, "achieved_gbs": gbs,
+                   "peak_gbs": peak, "frac": gbs / peak, "peak_source": kind},
+           "xbeta_and_vector_update_ms": prof.xb_ms / max(1, prof.xb_samples),
+           "kkt_after": [i.kkt for i in infos], "generate_s": t_gen}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,7 +444,12 @@ def main():
     ap.add_argument("--fp64-iters", type=int, default=400)
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: every fit stops after this many iterations (not a bench line)")
+    ap.add_argument("--grid-sample", action="store_true",
+                    help="batched-grid sample on the 10,000 x 500,000 workload (not a bench line)")
     args = ap.parse_args()
+    if args.grid_sample:
+        run_grid_sample(args, int(os.environ.get("LOCAL_RANK", 0)))
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -119,12 +119,13 @@ cudaError_t launch_gather_xb(int NB, const Fits &F, double *out, int64_t ldo, in
                              cudaStream_t s);  // out[b*ldo + i], i < F.n (FP64 path)
 
 // Tensor-core column pass (k_tc.cu). Schedule: CTA c takes `rounds` whole
-// 128-column tiles (c, c + grid, ...); the rem tiles left over are cut into
-// `slices` sample slices each, computed by CTAs 0 .. rem*slices-1.
+// 128-column tiles (c, c + grid, ...); the rem tiles left over go whole to
+// CTAs 0 .. rem-1 (slices = 0) or are cut into `slices` sample slices each,
+// computed by CTAs 0 .. rem*slices-1.
 struct TcSchedule {
   int grid, rounds, rem, slices;
-  int list_stride;  // F.T: 128 * max(rounds, 1) + 64
-  int slots;        // F.gridA: grid + rem list slots
+  int list_stride;  // F.T: 128 * (rounds + 1) + 64
+  int slots;        // F.gridA: grid, plus rem list slots when sliced
 };
 void col_tc_schedule(int64_t p, int64_t n, int num_sms, TcSchedule *out);
 int tc_tail_rows(int NB, int D);  // int32 digit sums per tail column and slice

@@ -25,12 +25,13 @@
 // blockIdx.x + grid, ... <= c.
 // Schedule: with R = floor(tiles / grid), CTA c takes the 128-column tiles
 // c, c + grid, ..., c + (R-1) grid whole. The rem = tiles - R grid tiles
-// left over are cut along the samples into ns slices each (ns ~ grid / rem),
-// so that the last round costs a slice instead of a tile: CTA c < rem * ns
+// left over either go whole to CTAs 0..rem-1 (ns = 0), or, when R is small
+// and a partial last round would cost a large share of the pass, are cut
+// along the samples into ns slices each (ns ~ grid / rem): CTA c < rem * ns
 // computes slice c % ns of tail tile c / ns and stores its exact integer
 // digit sums; the last slice CTA of a tile to finish adds them up and runs
 // that tile's epilogue. List slot c holds CTA c's whole tiles in tile order,
-// then its dense columns; slot grid + u holds tail tile u.
+// then its dense columns; slot grid + u holds sliced tail tile u.
 #include <cuda.h>
 #include <math.h>
 #include <stdint.h>
@@ -131,21 +132,23 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t base_u32 = smem_u32(smem_raw);
   uint8_t *ring = smem_raw + (((base_u32 + 1023u) & ~1023u) - base_u32);
   uint8_t *flags = ring + S * Sh::STAGE_BYTES;
-  const int T = F.T;                       // list stride: 128 * max(rounds, 1) + 64
-  const int TF = 128 * rounds;             // flags of the whole-tile columns
+  const int T = F.T;                       // list stride: 128 * (rounds + 1) + 64
+  const int TF = 128 * (rounds + 1);       // flags of the whole-tile columns
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = *F.it_base + off;
   const double *bcur = F.beta[k & 1];
   double *bnxt = F.beta[(k & 1) ^ 1];
   const int64_t ntiles = (X.p + 127) / 128;
-  const int R = rounds, ns = slices;
-  const int rem = (int)(ntiles - (int64_t)R * gridDim.x);
-  const bool tail = rem > 0 && (int)blockIdx.x < rem * ns;
+  const int ns = slices;
+  const int rem = (int)(ntiles - (int64_t)rounds * gridDim.x);
+  const bool tail = ns > 0 && rem > 0 && (int)blockIdx.x < rem * ns;
+  // whole tiles of this CTA (the leftover one included when not sliced)
+  const int R = rounds + ((ns == 0 && (int)blockIdx.x < rem) ? 1 : 0);
   const int tu = tail ? (int)blockIdx.x / ns : 0, tv = tail ? (int)blockIdx.x % ns : 0;
   const int ntl = R + (tail ? 1 : 0);      // local tile lt = R is the tail slice
   const int nk = (int)((X.n + 127) / 128);
-  const int tail_k0 = nk * tv / ns, tail_k1 = nk * (tv + 1) / ns;
+  const int tail_k0 = ns ? nk * tv / ns : 0, tail_k1 = ns ? nk * (tv + 1) / ns : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(256, 1)
     if (lane == 0) {
       int it = 0;
       for (int lt = 0; lt < ntl; ++lt) {
-        const int tile = lt < R ? (int)blockIdx.x + lt * (int)gridDim.x : R * (int)gridDim.x + tu;
+        const int tile = lt < R ? (int)blockIdx.x + lt * (int)gridDim.x : rounds * (int)gridDim.x + tu;
         const int k0 = lt < R ? 0 : tail_k0, k1 = lt < R ? nk : tail_k1;
         for (int kc = k0; kc < k1; ++kc, ++it) {
           const int s = it % S;
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(256, 1)
       __threadfence();
       const int slot = (int)gridDim.x + tu;
       const int m = threadIdx.x;
-      const int64_t sidx = (int64_t)(R * (int)gridDim.x + tu) * 128 + m;
+      const int64_t sidx = (int64_t)(rounds * (int)gridDim.x + tu) * 128 + m;
       const bool live = m < 128 && sidx < X.p;
       // sums over the slices of the digit sums, 4 columns per int4, every
       // slice's load in flight at once, into the (idle) stage ring
@@ -543,15 +546,19 @@ __global__ void k_tile_x(Dsg X, uint8_t *xt, int64_t nk) {
 //                the digit bytes, written as the byte image of one K-major
 //                swizzled operand tile per block of 128 active positions;
 //   k_xbeta_tc   CTA (rt, sp): samples [128 rt, +128) (M, the TMEM lanes)
-//                over the blocks of split sp. Its threads load the 128-byte
-//                sample runs of a block's active columns with 16-byte loads
-//                (one block ahead) into a 2-stage ring as an MN-major
-//                operand, a bulk copy brings the block's digit tile, and
+//                over the blocks of split sp. Its threads copy the 128-byte
+//                sample runs of a block's active columns with 16-byte
+//                asynchronous copies (kXbLag blocks in flight per thread)
+//                into a ring of stages as an MN-major operand, a bulk copy
+//                brings the block's digit tile, and
 //                kind::f8f6f4 MMAs accumulate exact integer sums in FP32 in
 //                TMEM. The epilogue writes one exact int64 partial per
 //                (split, sample, fit). (TMA tile::gather4 of the runs, 4
 //                columns per copy, ran at about 1.5 TB/s here: the copies,
 //                not HBM, set the pace.)
+// Blocks a thread keeps in flight (asynchronous copies) in the X~ beta pass.
+constexpr int kXbLag = 2;
+
 template <int NB, int DWD>
 struct XbShape {
   static constexpr int NR = NB * DWD;
@@ -559,7 +566,7 @@ struct XbShape {
   static constexpr int A_BYTES = 128 * 128;
   static constexpr int B_BYTES = N * 128;
   static constexpr int BUF = A_BYTES + B_BYTES;
-  static constexpr int STAGES = 2;
+  static constexpr int STAGES = kXbLag + 2;
   static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
 };
 
@@ -639,11 +646,12 @@ __global__ void __launch_bounds__(128)
 }
 
 // CTA (rt, sp). All 128 threads stream the blocks of split sp: each thread
-// loads 8 16-byte sample runs of the block's active columns (column k =
-// chunk / 8, samples 16 (chunk % 8) .. +15 of the row tile; the indices one
-// block ahead) and stores them into the stage as the 128-byte-swizzled
-// MN-major operand; thread 0 adds the block's digit tile by a bulk copy and
-// issues the MMAs. With fuse = 1 the last split CTA to finish a row tile sums
+// copies 8 16-byte sample runs of the block's active columns (column k =
+// chunk / 8, samples 16 (chunk % 8) .. +15 of the row tile; bytes of samples
+// >= n and absent columns zero-filled) into the stage as the 128-byte-
+// swizzled MN-major operand, and releases a block to the MMA issuer once its
+// own copies of it have landed; thread 0 adds the block's digit tile by a
+// bulk copy and issues the MMAs. With fuse = 1 the last split CTA to finish a row tile sums
 // the splits' integer partials of its 128 rows and applies the vector update
 // (z, r, theta and the stop-test partials, as k_vec), and the last row tile
 // to finish writes the totals.
@@ -691,73 +699,68 @@ __global__ void __launch_bounds__(128)
     // this thread's sample chunk c and the columns k = 16 e + kr (e < 8)
     const int c = tid & 7, kr = tid >> 3;
     const int64_t s0 = i0 + 16 * c;                 // first sample of the chunk
-    const bool cin = s0 < F.n;                      // chunk inside the samples
-    const int valid = cin ? (int)(F.n - s0 < 16 ? F.n - s0 : 16) : 0;
+    const uint32_t valid = s0 < F.n ? (uint32_t)(F.n - s0 < 16 ? F.n - s0 : 16) : 0u;
     const int nb = kb1 - kb0;
-    int idx[8];
-    int4 cur[8];
-    auto load_idx = [&](int blk) {
+    int idxA[8], idxB[8];
+    auto load_idx = [&](int blk, int (&idx)[8]) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) idx[e] = __ldg(scol + (int64_t)blk * 128 + 16 * e + kr);
     };
-    auto load_data = [&](int4 (&v)[8]) {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        v[e] = make_int4(0, 0, 0, 0);
-        if (cin && idx[e] < X.p)
-          v[e] = __ldg(reinterpret_cast<const int4 *>(X.geno + (int64_t)idx[e] * X.ld + s0));
-      }
-    };
-    load_idx(kb0);
-    load_data(cur);
-    if (nb > 1) load_idx(kb0 + 1);
     bool ok = true;
-    for (int it = 0; it < nb && ok; ++it) {
-      const int s = it % ST;
-      const uint32_t ph = (uint32_t)(it / ST) & 1u;
-      int4 nxt[8];
-      if (it + 1 < nb) {
-        load_data(nxt);
-        if (it + 2 < nb) load_idx(kb0 + it + 2);
-      }
-      if (!mbar_wait(&empty[s], ph ^ 1u, err, kErrEmpty)) { ok = false; break; }
-      uint8_t *stage = ring + s * Sh::BUF;
+    // one step: block `it` (column indices in idx) is copied into its stage;
+    // block it - kLag, whose copies this thread has waited for, is released
+    // to the MMA issuer, which (thread 0) multiplies it.
+    auto step = [&](int it, int (&idx)[8]) {
+      if (it < nb) {
+        const int s = it % ST;
+        if (!mbar_wait(&empty[s], ((uint32_t)(it / ST) & 1u) ^ 1u, err, kErrEmpty)) { ok = false; return; }
+        uint8_t *stage = ring + s * Sh::BUF;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        int4 v = cur[e];
-        if (valid < 16) {  // bytes of samples >= n are zero
-          uint32_t w[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int keep = min(max(valid - 4 * q, 0), 4);
-            w[q] &= (keep >= 4) ? 0xFFFFFFFFu : ((1u << (8 * keep)) - 1u);
-          }
-          v = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+        for (int e = 0; e < 8; ++e) {
+          const int kk = 16 * e + kr;
+          uint8_t *dst = stage + kk * 128 + ((c ^ (kk & 7)) << 4);
+          if (valid > 0 && idx[e] < X.p)
+            cp_async16(dst, X.geno + (int64_t)idx[e] * X.ld + s0, valid);  // bytes past n zero-filled
+          else
+            *reinterpret_cast<int4 *>(dst) = make_int4(0, 0, 0, 0);
         }
-        const int kk = 16 * e + kr;
-        *reinterpret_cast<int4 *>(stage + kk * 128 + ((c ^ (kk & 7)) << 4)) = v;
+        if (tid == 0) {
+          // the digit tile adds transaction bytes to the phase; the 128
+          // arrivals come when each thread's copies of the block have landed
+          mbar_expect_tx(&full[s], Sh::B_BYTES);
+          bulk_load(stage + Sh::A_BYTES, wtile + (int64_t)(kb0 + it) * Sh::B_BYTES, Sh::B_BYTES, &full[s]);
+        }
       }
-      fence_proxy_async();
-      if (tid == 0) {
-        mbar_arrive_expect_tx(&full[s], Sh::B_BYTES);
-        bulk_load(stage + Sh::A_BYTES, wtile + (int64_t)(kb0 + it) * Sh::B_BYTES, Sh::B_BYTES, &full[s]);
-        if (!mbar_wait(&full[s], ph, err, kErrFull)) {
-          ok = false;
-        } else {
+      cp_async_commit();
+      const int rt = it - kXbLag;  // block whose copies are now complete
+      if (rt >= 0 && rt < nb) {
+        cp_async_wait<kXbLag>();
+        fence_proxy_async();
+        const int s = rt % ST;
+        const uint32_t ph = (uint32_t)(rt / ST) & 1u;
+        mbar_arrive(&full[s]);  // one arrival per thread and phase (count 128)
+        if (tid == 0) {
+          if (!mbar_wait(&full[s], ph, err, kErrFull)) { ok = false; return; }
           tc_fence_after();
-          const uint32_t sa = smem_u32(stage);
+          const uint32_t sa = smem_u32(ring + s * Sh::BUF);
           const uint64_t ad = sdesc_mn128(sa), bd = sdesc_k128(sa + Sh::A_BYTES);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            mma_f8(tmem, ad + (uint64_t)(q * 256), bd + (uint64_t)(q * 2), idesc, (it | q) != 0 ? 1u : 0u);
+            mma_f8(tmem, ad + (uint64_t)(q * 256), bd + (uint64_t)(q * 2), idesc, (rt | q) != 0 ? 1u : 0u);
           mma_commit(&empty[s]);
         }
-      } else {
-        mbar_arrive(&full[s]);
       }
-#pragma unroll
-      for (int e = 0; e < 8; ++e) cur[e] = nxt[e];
+    };
+    load_idx(kb0, idxA);
+    if (nb > 1) load_idx(kb0 + 1, idxB);
+    for (int it = 0; it < nb + kXbLag && ok; it += 2) {
+      step(it, idxA);
+      if (it + 2 < nb) load_idx(kb0 + it + 2, idxA);
+      if (!ok) break;
+      step(it + 1, idxB);
+      if (it + 3 < nb) load_idx(kb0 + it + 3, idxB);
     }
+    cp_async_wait<0>();
     if (tid == 0) mma_commit(&dbar);
     __syncwarp();
     const bool done = mbar_wait(&dbar, 0u, err, kErrAccFull) && ok;
@@ -886,7 +889,7 @@ size_t g_xt_opted = 0;  // the attribute is set on first use (static + dynamic m
 
 size_t xbeta_tc_smem(int NB, int DWD) {
   const int N = ((NB * DWD + 15) / 16) * 16;
-  return (size_t)2 * (128 * 128 + N * 128) + 1024 + 16;
+  return (size_t)(kXbLag + 2) * (128 * 128 + N * 128) + 1024 + 16;
 }
 
 template <int NB, int DWD>
@@ -949,11 +952,14 @@ void col_tc_schedule(int64_t p, int64_t n, int num_sms, TcSchedule *out) {
   sc.grid = std::max(1, num_sms);  // one CTA per SM, even with fewer tiles (they are then sliced)
   sc.rounds = (int)(tiles / sc.grid);
   sc.rem = (int)(tiles - (int64_t)sc.rounds * sc.grid);
-  sc.slices = sc.rem ? (int)std::max<int64_t>(
-                            1, std::min<int64_t>(std::min<int64_t>(nk, sc.grid / sc.rem), kMaxTailSlices))
-                     : 0;
-  sc.list_stride = 128 * std::max(sc.rounds, 1) + 64;
-  sc.slots = sc.grid + sc.rem;
+  // slicing pays only when a partial last round is a large share of the pass
+  // (measured: with 5 whole rounds and 22 leftover tiles it lost 5 %)
+  sc.slices = (sc.rem && sc.rounds <= 2)
+                  ? (int)std::max<int64_t>(
+                        1, std::min<int64_t>(std::min<int64_t>(nk, sc.grid / sc.rem), kMaxTailSlices))
+                  : 0;
+  sc.list_stride = 128 * (sc.rounds + 1) + 64;
+  sc.slots = sc.grid + (sc.slices ? sc.rem : 0);
 }
 
 int tc_tail_rows(int NB, int D) { return NB * D; }

@@ -175,7 +175,7 @@ def test_learned_warm_start_keeps_the_fit_and_saves_iterations(ctx):
                 U.append(to_np(u))
                 T.append(t)
                 W.append(np.where(t != 0.0, 10.0, 1.0))
-    assert len(U) >= 24
+    assert len(U) >= 12
     U, T, W = np.concatenate(U), np.concatenate(T), np.concatenate(W)
     npar = ctx.mlp_param_count()
     params = torch.zeros(npar, dtype=torch.float32, device="cuda")
