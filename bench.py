@@ -132,6 +132,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """Largest value of x over the ranks (x itself without torch.distributed):
+    the timed region of a multi-rank run is its slowest rank's."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_workload():
     from paper_2601_02826_gb300 import synth
     return synth.geno_int8()
@@ -193,10 +204,7 @@ def run_gb300(args, rank, world, local_rank):
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
     prof = ctx.profile(enable=False)
-    ms_t = torch.tensor([ms], device=dev)
-    if dist:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, dev)
     fits = B * args.steps * world
     value = fits / (ms_max / 1e3)
 
@@ -256,7 +264,7 @@ def run_gb300(args, rank, world, local_rank):
         for _ in range(n_e2e):
             ctx.fit_batch(dh, yh, TAUS, lam, oh, bp, bh, zh, thh, opts=mixed, host=True)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
+        te = max_over_ranks(time.perf_counter() - t0, dev)
         h2d = gh.numel() + 8 * (ch.numel() + yh.numel() + oh.numel())
         d2h = 8 * (bh.numel() + zh.numel() + thh.numel())
         e2e = {"value": B * n_e2e * world / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -73,8 +73,10 @@ extern "C" {
                              X~^T theta on the tensor cores with theta split
                              into base-16 digits (E4M3) against the genotype
                              codes read as E4M3, FP32 accumulation that stays
-                             exact; X~ beta from int8 digits of a_j beta_j by
-                             DP4A with int64 sums. int8 storage only. */
+                             exact; X~ beta likewise from base-16 digits of
+                             a_j beta_j over the active columns, int64 sums.
+                             int8 storage only; tensor cores with <= 63
+                             covariates, else the kernels of FSQR_MIXED_SIMT. */
 #define FSQR_MIXED_SIMT 2 /* as FSQR_MIXED, with X~^T theta from int8 digits of
                              theta by DP4A on the SIMT cores instead */
 
@@ -83,6 +85,10 @@ extern "C" {
 #define FSQR_WARM_GIVEN 1 /* beta, z, theta arrays are read as the start */
 #define FSQR_WARM_PATH 2  /* fsqr_fit_batch only: along each tau's lambda path,
                              fit l starts from fit l-1's solution (Section 7) */
+#define FSQR_WARM_LEARNED 3 /* every fit starts from the learned warm start of the
+                               network opts.warm_params (fsqr_warm_start at
+                               lambda / lambda_max(tau)); beta, z, theta are
+                               overwritten by that start, then by the fit */
 
 typedef struct fsqr_ctx fsqr_ctx;
 
@@ -118,6 +124,8 @@ typedef struct {
                              default 4 */
   int32_t max_group;      /* fits advanced together per X pass, 1..8; default 4 */
   int64_t timeout_ms;     /* > 0: stop with FSQR_ETIMEOUT after this wall time */
+  const float *warm_params; /* device, fsqr_mlp_param_count() floats: the network of
+                               FSQR_WARM_LEARNED; default NULL */
 } fsqr_opts;
 
 /* Per-fit report. */

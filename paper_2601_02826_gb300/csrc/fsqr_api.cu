@@ -397,8 +397,10 @@ int check_opts(fsqr_ctx *ctx, const fsqr_opts *o, int G) {
   if (o->check_every < 1) return fail(ctx, FSQR_EINVAL, "check_every must be >= 1");
   if (o->precision != FSQR_FP64 && o->precision != FSQR_MIXED && o->precision != FSQR_MIXED_SIMT)
     return fail(ctx, FSQR_EINVAL, "unknown precision %d", o->precision);
-  if (o->warm < FSQR_WARM_NONE || o->warm > FSQR_WARM_PATH)
+  if (o->warm < FSQR_WARM_NONE || o->warm > FSQR_WARM_LEARNED)
     return fail(ctx, FSQR_EINVAL, "unknown warm mode %d", o->warm);
+  if (o->warm == FSQR_WARM_LEARNED && !o->warm_params)
+    return fail(ctx, FSQR_EINVAL, "FSQR_WARM_LEARNED needs opts.warm_params");
   if (o->precision != FSQR_FP64 && (o->digits < 3 || o->digits > 5))
     return fail(ctx, FSQR_EINVAL, "digits must be in 3..5");
   if (o->max_group < 1 || o->max_group > kMaxNB)
@@ -777,6 +779,10 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   return timed_out ? FSQR_ETIMEOUT : FSQR_OK;
 }
 
+int warm_start_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, double frac,
+                    const double *omega, const float *params, double ysd, double *beta, double *z,
+                    double *theta);
+
 int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_tau,
                    const double *taus, int n_lambda, const double *lambdas, const double *omega,
                    const int64_t *block_ptr, int G, const fsqr_opts *opts, double *beta, double *z,
@@ -822,6 +828,14 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
   }
   std::vector<double> lmax(n_tau);
   for (int t = 0; t < n_tau; ++t) TRY(lambda_max_impl(ctx, pr, y, taus[t], omega, &lmax[t]));
+  if (opts->warm == FSQR_WARM_LEARNED)
+    for (int t = 0; t < n_tau; ++t)
+      for (int l = 0; l < n_lambda; ++l) {
+        const int f = t * n_lambda + l;
+        const double frac = lmax[t] > 0.0 ? lambdas[f] / lmax[t] : 1.0;
+        TRY(warm_start_impl(ctx, pr, y, taus[t], frac, omega, opts->warm_params, ysd, beta + (int64_t)f * P,
+                            z + (int64_t)f * n, theta + (int64_t)f * n));
+      }
 
   SolveEnv E{};
   E.pr = &pr;
@@ -876,7 +890,7 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
         gs.lam[q] = lambdas[f];
         gs.lamnorm[q] = lmax[t] > 0.0 ? lmax[t] : 1.0;
         gs.fit[q] = f;
-        gs.src_fit[q] = (opts->warm == FSQR_WARM_GIVEN) ? f : -1;
+        gs.src_fit[q] = (opts->warm == FSQR_WARM_GIVEN || opts->warm == FSQR_WARM_LEARNED) ? f : -1;
       }
       groups.push_back(gs);
     }
@@ -1305,6 +1319,27 @@ int warm_features_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double ta
   return FSQR_OK;
 }
 
+// The start the network proposes for (tau, frac * lambda_max(tau)): beta (P),
+// z (n), theta (n) on the device; ysd = sd(y).
+int warm_start_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, double frac,
+                    const double *omega, const float *params, double ysd, double *beta, double *z,
+                    double *theta) {
+  const Dsg &X = pr.X;
+  float *u, *f;
+  double *xb;
+  TRY(wsget(ctx, "warm_u", (size_t)std::max<int64_t>(1, X.P - 1) * kMlpIn, &u));
+  TRY(wsget(ctx, "warm_f", (size_t)std::max<int64_t>(1, X.P - 1), &f));
+  TRY(wsget(ctx, "warm_xb", (size_t)X.n, &xb));
+  LmaxDev L;
+  TRY(warm_features_impl(ctx, pr, y, tau, frac, omega, u, &L));
+  if (X.P > 1) TRY(mlp_forward_chunked(ctx, params, u, X.P - 1, f));
+  LK(launch_warm_beta(f, X.P, L.q, ysd, beta, ctx->stream));
+  TRY(predict_impl(ctx, pr, beta, 1, xb));
+  LK(launch_warm_dual(y, xb, X.n, tau, z, theta, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSQR_OK;
+}
+
 int check_warm_args(fsqr_ctx *ctx, const double *y, double tau, double frac, const double *omega) {
   if (!y || !omega) return fail(ctx, FSQR_EINVAL, "NULL argument");
   if (!(tau > 0.0 && tau < 1.0)) return fail(ctx, FSQR_EINVAL, "tau must be in (0,1)");
@@ -1414,22 +1449,9 @@ int fsqr_warm_start(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, doubl
   if (!params || !beta || !z || !theta) return fail(ctx, FSQR_EINVAL, "NULL argument");
   Prep pr;
   TRY(prepare(ctx, Xd, &pr, false));
-  const Dsg &X = pr.X;
   double ymax = 0.0, ysd = 0.0;
-  TRY(y_stats(ctx, y, X.n, &ymax, &ysd));
-  float *u, *f;
-  double *xb;
-  TRY(wsget(ctx, "warm_u", (size_t)std::max<int64_t>(1, X.P - 1) * kMlpIn, &u));
-  TRY(wsget(ctx, "warm_f", (size_t)std::max<int64_t>(1, X.P - 1), &f));
-  TRY(wsget(ctx, "warm_xb", (size_t)X.n, &xb));
-  LmaxDev L;
-  TRY(warm_features_impl(ctx, pr, y, tau, lam_frac, omega, u, &L));
-  if (X.P > 1) TRY(mlp_forward_chunked(ctx, params, u, X.P - 1, f));
-  LK(launch_warm_beta(f, X.P, L.q, ysd, beta, ctx->stream));
-  TRY(predict_impl(ctx, pr, beta, 1, xb));
-  LK(launch_warm_dual(y, xb, X.n, tau, z, theta, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  return FSQR_OK;
+  TRY(y_stats(ctx, y, pr.X.n, &ymax, &ysd));
+  return warm_start_impl(ctx, pr, y, tau, lam_frac, omega, params, ysd, beta, z, theta);
 }
 
 }  // extern "C"

@@ -35,7 +35,7 @@ class Opts(C.Structure):
                 ("mu", C.c_double), ("eta", C.POINTER(C.c_double)), ("eta_margin", C.c_double),
                 ("power_iters", C.c_int32), ("power_tol", C.c_double), ("precision", C.c_int32),
                 ("warm", C.c_int32), ("digits", C.c_int32), ("max_group", C.c_int32),
-                ("timeout_ms", C.c_int64)]
+                ("timeout_ms", C.c_int64), ("warm_params", C.c_void_p)]
 
 
 class Info(C.Structure):

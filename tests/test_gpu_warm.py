@@ -215,3 +215,23 @@ def test_learned_warm_start_keeps_the_fit_and_saves_iterations(ctx):
     print("learned warm start: (seed, tau, frac, cold iters, learned iters)", report,
           f"total {cold_it} -> {warm_it} ({warm_it / cold_it:.3f}x)")
     assert warm_it < cold_it
+
+    # the same start requested through fsqr_fit_batch (FSQR_WARM_LEARNED)
+    w = synth.tiny_geno(301, 300, 800, c=0, fmt=synth.FMT_INT8, G=4)
+    dw = _up(ctx, w)
+    d = O.build_design(O.decode_stored(w.geno, w.fmt, w.n), w.cov)
+    taus2, fr2 = [0.35, 0.6], [0.4, 0.3]
+    lmaxs = [O.lambda_max(d.Xt, w.y, t, w.omega) for t in taus2]
+    lams = np.array([[f * lm for f in fr2] for lm in lmaxs])
+    beta = torch.zeros(4 * w.P, dtype=torch.float64, device="cuda")
+    z = torch.zeros(4 * w.n, dtype=torch.float64, device="cuda")
+    th = torch.zeros(4 * w.n, dtype=torch.float64, device="cuda")
+    rc, infos = ctx.fit_batch(dw.design, dw.y, taus2, lams, dw.omega, w.block_ptr(), beta, z, th,
+                              opts=dict(tol=1e-6, max_iter=1_000_000, warm=3, warm_params=params.data_ptr()))
+    assert rc == 0
+    bb, zz, tt = to_np(beta).reshape(4, -1), to_np(z).reshape(4, -1), to_np(th).reshape(4, -1)
+    for ti, tau in enumerate(taus2):
+        for li in range(2):
+            f = ti * 2 + li
+            lam = lams[ti, li] * w.omega
+            assert O.kkt(d.Xt, w.y, tau, lam, lmaxs[ti], bb[f], zz[f], tt[f]).value <= 1.001e-6
