@@ -217,7 +217,7 @@ int prepare(fsqr_ctx *ctx, const fsqr_design *d, Prep *pp, bool need_colbound) {
   if (hmiss > 0)
     return fail(ctx, FSQR_EINVAL,
                 "%d missing genotype entries: mean imputation of missing entries is not "
-                "supported by this build",
+                "supported by this library",
                 hmiss);
   return FSQR_OK;
 }
@@ -1574,7 +1574,7 @@ int fsqr_lambda_max_noalloc(fsqr_ctx *ctx, const fsqr_design *d, const double *y
   if (hmiss > 0)
     return fail(ctx, FSQR_EINVAL,
                 "%d missing genotype entries: mean imputation of missing entries is not "
-                "supported by this build",
+                "supported by this library",
                 hmiss);
   const int64_t n = X.n, npad = pad16(n);
   int64_t k = (int64_t)ceil((double)n * tau);
