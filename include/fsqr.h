@@ -122,7 +122,11 @@ typedef struct {
   int32_t digits;         /* FSQR_MIXED_SIMT: int8 (7-bit) digits per theta entry, 3..5;
                              FSQR_MIXED uses 7 base-16 digits (6 when digits == 3);
                              default 4 */
-  int32_t max_group;      /* fits advanced together per X pass, 1..8; default 4 */
+  int32_t max_group;      /* fits advanced together per X pass, 1..8, or 0: chosen by
+                             timing the candidates 1, 2, 3, 4 and min(B, 8) on the
+                             first fits (a short cold run of each, cached per context
+                             and problem shape; fsqr_profile.tuned_group reports it);
+                             default 4 */
   int64_t timeout_ms;     /* > 0: stop with FSQR_ETIMEOUT after this wall time */
   const float *warm_params; /* device, fsqr_mlp_param_count() floats: the network of
                                FSQR_WARM_LEARNED; default NULL */
@@ -246,6 +250,7 @@ typedef struct {
   int64_t iterations;                    /* FS-QRPPA steps executed */
   int64_t kernel_launches;
   int64_t col_bytes;                     /* algorithmic bytes of the last column pass */
+  int64_t tuned_group;                   /* group size the autotuner chose last (0: none) */
 } fsqr_profile;
 
 int fsqr_profile_enable(fsqr_ctx *ctx, int on);

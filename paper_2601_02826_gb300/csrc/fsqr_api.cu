@@ -26,6 +26,7 @@ struct fsqr_ctx {
   int num_sms = 0;
   std::string err;
   std::map<std::string, std::pair<void *, size_t>> ws;
+  std::map<std::string, int> tuned;  // autotuned fits per X pass, by problem shape
   double *hpin = nullptr;  // pinned host scratch
   size_t hpin_n = 0;
   bool prof = false;
@@ -403,8 +404,8 @@ int check_opts(fsqr_ctx *ctx, const fsqr_opts *o, int G) {
     return fail(ctx, FSQR_EINVAL, "FSQR_WARM_LEARNED needs opts.warm_params");
   if (o->precision != FSQR_FP64 && (o->digits < 3 || o->digits > 5))
     return fail(ctx, FSQR_EINVAL, "digits must be in 3..5");
-  if (o->max_group < 1 || o->max_group > kMaxNB)
-    return fail(ctx, FSQR_EINVAL, "max_group must be in 1..8");
+  if (o->max_group < 0 || o->max_group > kMaxNB)
+    return fail(ctx, FSQR_EINVAL, "max_group must be in 0..8");
   if (o->eta)
     for (int g = 0; g < G; ++g)
       if (!(o->eta[g] > 0.0) || isinf(o->eta[g]))
@@ -783,6 +784,96 @@ int warm_start_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, 
                     const double *omega, const float *params, double ysd, double *beta, double *z,
                     double *theta);
 
+// Autotuner of the fits advanced together per X pass (opts.max_group = 0).
+// For each candidate g (1, 2, 3, 4 and min(B, 8), up to B), the first g
+// fits run cold for I1 and then I2 iterations; the difference of the two
+// wall times over I2 - I1 is the time per iteration t(g) without the set-up,
+// and the g with the least ceil(B / g) t(g) is chosen. The integer and FP64
+// results do not depend on g. The users' arrays of those fits are saved and
+// restored around the runs; the choice is cached per context and shape.
+int tune_group(fsqr_ctx *ctx, const SolveEnv &E, int B, int n_lambda, const double *taus,
+               const double *lambdas, const std::vector<double> &lmax, int *out) {
+  const Dsg &X = E.pr->X;
+  const fsqr_opts *o = E.o;
+  char key[160];
+  snprintf(key, sizeof key, "%lld/%lld/%lld/%d/%d/%d/%d/%d", (long long)X.n, (long long)X.p, (long long)X.c,
+           X.fmt, o->precision, o->digits, B, o->warm);
+  auto it = ctx->tuned.find(key);
+  if (it != ctx->tuned.end()) {
+    *out = it->second;
+    ctx->pf.tuned_group = it->second;
+    return FSQR_OK;
+  }
+  std::vector<int> cand;
+  for (int g : {1, 2, 3, 4, std::min(B, kMaxNB)})
+    if (g <= B && (cand.empty() || g > cand.back())) cand.push_back(g);
+  const int gmax = cand.back();
+  if (cand.size() == 1) {
+    *out = gmax;
+    ctx->pf.tuned_group = gmax;
+    return FSQR_OK;
+  }
+  const int64_t P = X.P, n = X.n;
+  // save the first gmax fits' arrays (starts of FSQR_WARM_GIVEN / LEARNED)
+  double *sv_b, *sv_z, *sv_t;
+  TRY(wsget(ctx, "tune_b", (size_t)(gmax * P), &sv_b));
+  TRY(wsget(ctx, "tune_z", (size_t)(gmax * n), &sv_z));
+  TRY(wsget(ctx, "tune_t", (size_t)(gmax * n), &sv_t));
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(sv_b, E.beta, sizeof(double) * gmax * P, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(sv_z, E.z, sizeof(double) * gmax * n, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(sv_t, E.theta, sizeof(double) * gmax * n, cudaMemcpyDeviceToDevice, st));
+  std::vector<fsqr_info> scratch((size_t)B);
+  fsqr_opts tmp = *o;
+  tmp.tol = 0.0;
+  tmp.timeout_ms = 0;
+  SolveEnv E2 = E;
+  E2.o = &tmp;
+  E2.infos = scratch.data();
+  E2.deadline_ms = 0.0;
+  const int K = std::max(1, o->check_every);
+  const int I1 = K * std::max(1, 20 / K), I2 = I1 + K * std::max(1, 80 / K);
+  double best = 0.0;
+  int bestg = cand[0];
+  const fsqr_profile keep = ctx->pf;
+  for (int g : cand) {
+    GroupSpec gs{};
+    gs.nb = g;
+    for (int q = 0; q < g; ++q) {
+      const int t = q / n_lambda;
+      gs.tau[q] = taus[t];
+      gs.lam[q] = lambdas[q];
+      gs.lamnorm[q] = lmax[t] > 0.0 ? lmax[t] : 1.0;
+      gs.fit[q] = q;
+      gs.src_fit[q] = -1;
+    }
+    double w[2];
+    for (int r = 0; r < 2; ++r) {
+      tmp.max_iter = r == 0 ? I1 : I2;
+      CK(cudaStreamSynchronize(st));
+      const double t0 = now_ms();
+      TRY(solve_group(ctx, E2, gs));
+      CK(cudaStreamSynchronize(st));
+      w[r] = now_ms() - t0;
+    }
+    const double per_iter = std::max(w[1] - w[0], 1e-6) / (double)(I2 - I1);
+    const double cost = (double)((B + g - 1) / g) * per_iter;
+    if (g == cand[0] || cost < best) { best = cost; bestg = g; }
+  }
+  // the timing runs' kernels count as launches; their samples do not enter the profile
+  const int64_t launches = ctx->pf.kernel_launches;
+  ctx->pf = keep;
+  ctx->pf.kernel_launches = launches;
+  CK(cudaMemcpyAsync(E.beta, sv_b, sizeof(double) * gmax * P, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(E.z, sv_z, sizeof(double) * gmax * n, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(E.theta, sv_t, sizeof(double) * gmax * n, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->tuned[key] = bestg;
+  ctx->pf.tuned_group = bestg;
+  *out = bestg;
+  return FSQR_OK;
+}
+
 int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_tau,
                    const double *taus, int n_lambda, const double *lambdas, const double *omega,
                    const int64_t *block_ptr, int G, const fsqr_opts *opts, double *beta, double *z,
@@ -863,7 +954,8 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
 
   // groups of fits
   const int B = n_tau * n_lambda;
-  const int mg = opts->max_group;
+  int mg = opts->max_group;
+  if (mg == 0) TRY(tune_group(ctx, E, B, n_lambda, taus, lambdas, lmax, &mg));
   std::vector<GroupSpec> groups;
   if (opts->warm == FSQR_WARM_PATH) {
     for (int l = 0; l < n_lambda; ++l)

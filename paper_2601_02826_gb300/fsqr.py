@@ -53,7 +53,8 @@ class Info(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("col_samples", C.c_int64), ("col_ms", C.c_double), ("xb_samples", C.c_int64),
                 ("xb_ms", C.c_double), ("vec_samples", C.c_int64), ("vec_ms", C.c_double),
-                ("iterations", C.c_int64), ("kernel_launches", C.c_int64), ("col_bytes", C.c_int64)]
+                ("iterations", C.c_int64), ("kernel_launches", C.c_int64), ("col_bytes", C.c_int64),
+                ("tuned_group", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -217,6 +217,37 @@ def test_batch_of_eight_fits_on_tensor_cores(ctx):
             assert O.kkt(d.Xt, w.y, tau, lam, lmaxs[t_i], bb[f], zz[f], tt[f]).value <= 1.001e-6, f
 
 
+def test_autotuned_group_size(ctx):
+    """max_group = 0: the group size is chosen by timing the candidates on the
+    first fits; every fit still meets the oracle's stop test, and the choice
+    is cached for the next call on the same shape."""
+    w = synth.tiny_geno(107, 240, 600, c=1, fmt=synth.FMT_INT8, G=3, taus=(0.4,))
+    dw = _up(ctx, w)
+    d = O.build_design(O.decode_stored(w.geno, w.fmt, w.n), w.cov)
+    taus = [0.3, 0.5, 0.7]
+    fr = [0.5, 0.35]
+    lmaxs = [O.lambda_max(d.Xt, w.y, t, w.omega) for t in taus]
+    lams = np.array([[f * lm for f in fr] for lm in lmaxs])
+    B = 6
+    chosen = []
+    for _ in range(2):
+        beta = torch.zeros(B * w.P, dtype=torch.float64, device="cuda")
+        z = torch.zeros(B * w.n, dtype=torch.float64, device="cuda")
+        th = torch.zeros(B * w.n, dtype=torch.float64, device="cuda")
+        ctx.profile(enable=False, reset=True)
+        rc, infos = ctx.fit_batch(dw.design, dw.y, taus, lams, dw.omega, w.block_ptr(), beta, z, th,
+                                  opts=dict(tol=1e-6, max_iter=1_000_000, precision=1, max_group=0))
+        assert rc == 0
+        chosen.append(ctx.profile(enable=False).tuned_group)
+        bb, zz, tt = to_np(beta).reshape(B, -1), to_np(z).reshape(B, -1), to_np(th).reshape(B, -1)
+        for t_i, tau in enumerate(taus):
+            for l_i in range(len(fr)):
+                f = t_i * len(fr) + l_i
+                lam = lams[t_i, l_i] * w.omega
+                assert O.kkt(d.Xt, w.y, tau, lam, lmaxs[t_i], bb[f], zz[f], tt[f]).value <= 1.001e-6, f
+    assert chosen[0] in (1, 2, 3, 4, 6) and chosen[1] == chosen[0]
+
+
 def test_batch_grid_and_path_warm_start(ctx):
     w = synth.tiny_geno(105, 300, 400, c=1, fmt=synth.FMT_INT8, G=3, taus=(0.25, 0.75))
     dw = _up(ctx, w)
