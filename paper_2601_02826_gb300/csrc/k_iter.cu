@@ -1,14 +1,16 @@
 // FS-QRPPA inner iteration kernels (Section 4, eq. fsppa_update, Algorithm 1).
 //
-// One iteration k of a group of NB fits is four launches on one stream:
-//   [k_quantize]  theta^k -> int8 digit words            (FSQR_MIXED only)
+// One iteration k of a group of NB fits is these launches on one stream:
+//   [k_quantize]  theta^k -> int8 digit words            (mixed SIMT path only)
 //   k_col         s = X~^T theta^k over every column, the stop-test distance
 //                 for beta^k, and the block soft threshold of eq. beta_update
 //                 -> beta^{k+1}, per-CTA lists of columns with beta^{k+1} != 0
-//   k_xbeta       partial sums of X~ beta^{k+1} over those columns only
 //   [k_check]     stop test of the iterate w^k             (every K steps)
+//   k_xbeta       partial sums of X~ beta^{k+1} over those columns only
 //   k_vec         z^{k+1} (eq. z_update), r^{k+1}, theta^{k+1} (extrapolated
 //                 dual step mu/(G+1)) and the reductions for the next test.
+// The tensor-core path (k_tc.cu) replaces k_quantize, k_col and k_xbeta
+// with its own kernels and applies the k_vec update inside its X~ beta pass.
 // The G paper blocks survive as the per-block eta_g; the execution tiling
 // (CTAs over contiguous column ranges) is independent of them.
 #include <math.h>
