@@ -159,7 +159,7 @@ int fsqr_destroy(fsqr_ctx *ctx);
 /* Last error message of this context ("" if none); valid until the next call. */
 const char *fsqr_last_error(const fsqr_ctx *ctx);
 
-/* Column statistics (row A0 of the hot-path table; Section 7): mean and
+/* Column statistics (Section 7, standardisation of the features): mean and
  * population sd over non-missing entries of the c covariates and p feature
  * columns. mean_out/sd_out: device, length c+p. */
 int fsqr_col_stats(fsqr_ctx *ctx, const fsqr_design *X, double *mean_out, double *sd_out);
@@ -216,7 +216,8 @@ int fsqr_fit_batch_host(fsqr_ctx *ctx, const fsqr_design *X, const double *y, in
                         fsqr_info *infos);
 
 /* Stop-test residuals, primal value and duality gap of a given iterate
- * (row A8 of the hot-path table). y, omega, beta (P), z, theta (n): device.
+ * (the saddle-point conditions of Proposition 1 and the dual of the
+ * penalised problem). y, omega, beta (P), z, theta (n): device.
  * lambda_norm > 0 divides R_b. out: host. */
 int fsqr_kkt(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau, double lambda,
              const double *omega, double lambda_norm, const double *beta, const double *z,
