@@ -374,7 +374,11 @@ def run_reference(args, rank, world):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded Bin(2,MAF) genotypes, heteroscedastic normal noise)",
            "config": {"workload": "geno_int8", "n": w.n, "p": w.p, "covariates": w.c,
-                      "G": len(w.block_sizes), "taus": TAUS, "lambda": "0.1 lambda_max(tau)"},
+                      "G": len(w.block_sizes), "taus": TAUS, "lambda": "0.1 lambda_max(tau)",
+                      "fits_per_step": len(TAUS),
+                      "precision": "FP64 oracle (numpy, dense standardised design)",
+                      "parallelism": "rank 0 only (host cores)",
+                      "l2": "inputs larger than L2 (X = 500 MB int8)"},
            "impl": "reference",
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                             "sample": sample},
