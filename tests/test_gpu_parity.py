@@ -282,6 +282,26 @@ def test_batch_grid_and_path_warm_start(ctx):
                 assert infos[f].status == 0 and infos[f].lambda_max == pytest.approx(lmaxs[t_i], rel=1e-10)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lambda_above_lambda_max_gives_the_intercept_only_fit(ctx, precision):
+    """The degenerate end of the path: at lambda = 1.02 lambda_max every
+    penalised coefficient is exactly 0 at the converged iterate (a nonzero one
+    would leave R_beta near 0.02), and the objective is the intercept-only one
+    at the sample tau-quantile."""
+    w = CASES["int8"]()
+    tau = 0.3
+    d, lmax, lam_s, lam, mu, bp, eta = oracle_problem(w, tau, 1.02)
+    dw = _up(ctx, w)
+    rc, info, b, z, t = _run(ctx, dw, w, tau, lam_s, mu, eta, 400000, tol=1e-6, precision=precision)
+    assert rc == 0
+    assert np.all(b[1:] == 0.0)
+    q = np.sort(w.y)[math.ceil(w.n * tau) - 1]
+    b0 = np.zeros(w.P)
+    b0[0] = q
+    assert O.objective(d.Xt, w.y, b, tau, lam) == pytest.approx(O.objective(d.Xt, w.y, b0, tau, lam), rel=1e-6)
+    assert O.kkt(d.Xt, w.y, tau, lam, lmax, b, z, t).value <= 1.001e-6
+
+
 def test_kkt_entry_point_matches_oracle(ctx):
     w = CASES["int8"]()
     tau = w.taus[0]
