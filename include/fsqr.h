@@ -76,8 +76,8 @@ extern "C" {
                              exact; X~ beta likewise from base-16 digits of
                              a_j beta_j over the active columns, int64 sums.
                              int8 storage only; tensor cores with <= 63
-                             covariates and n, p <= 2^20 (where the FP32
-                             digit sums stay exact), else the kernels of
+                             covariates, n <= 2^20 and p <= 2^19 (where
+                             the digit sums stay exact), else the kernels of
                              FSQR_MIXED_SIMT. */
 #define FSQR_MIXED_SIMT 2 /* as FSQR_MIXED, with X~^T theta from int8 digits of
                              theta by DP4A on the SIMT cores instead */

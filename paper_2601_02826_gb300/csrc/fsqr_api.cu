@@ -444,12 +444,13 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   const int64_t n = X.n, npad = pad16(n), P = X.P;
   const bool mixed = E.o->precision == FSQR_MIXED || E.o->precision == FSQR_MIXED_SIMT;
   // tensor-core passes: int8 storage, at most 63 covariates, <= 8 fits, and
-  // sizes for which every FP32 digit-product sum stays exact: a sum over n
-  // samples (or over the active columns of one X~ beta split, at most p) of
-  // products |g t| <= 16 is an integer multiple of 2^-9 below 2^24 * 2^-9
-  // when n, p <= 2^20
+  // sizes for which the integer arithmetic stays exact: a digit-product sum
+  // over n samples (or over the active columns of an X~ beta split, at most
+  // p) of |g t| <= 16 is a multiple of 2^-9 below 2^24 * 2^-9 in FP32 when
+  // n, p <= 2^20; the recombined X~ beta, sum_j g_ij W_j with |W_j| < 2^43,
+  // stays below 2^63 in int64 when p <= 2^19
   const bool tc = E.o->precision == FSQR_MIXED && X.fmt == FSQR_INT8 && X.p > 0 && X.c <= 63 && NB <= 8 &&
-                  X.n <= ((int64_t)1 << 20) && X.p <= ((int64_t)1 << 20);
+                  X.n <= ((int64_t)1 << 20) && X.p <= ((int64_t)1 << 19);
   const double t0 = now_ms();
   cudaStream_t st = ctx->stream;
 
