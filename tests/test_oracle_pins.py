@@ -416,3 +416,29 @@ def test_block_layouts():
     rng = np.random.default_rng(0)
     bs = synth.ragged_blocks(rng, 100_000, 5000, 30000)
     assert sum(bs) == 100_000 and all(b >= 1 for b in bs) and all(b <= 30000 for b in bs)
+
+
+def test_step_metric_makes_the_ppa_metric_positive_semidefinite():
+    """Reading of the step condition (Section 4): with eta_g = (1 + margin) mu
+    Lambda_max(X_g^T X_g) and sigma = mu/(G+1), D - sigma A^T A is positive
+    semidefinite for A = [X_1 .. X_G  I] and D = diag(eta_g I, mu I), which
+    makes the PPA metric H PSD. Below sigma Lambda_max it is not."""
+    w = synth.tiny_geno(33, 40, 30, c=0, fmt=synth.FMT_INT8, G=3)
+    d = O.build_design(O.decode_stored(w.geno, w.fmt, w.n), w.cov)
+    Xt, bp = d.Xt, w.block_ptr()
+    G = len(bp) - 1
+    mu = O.default_mu(w.y)
+    sigma = mu / (G + 1)
+    A = np.hstack([Xt, np.eye(w.n)])
+
+    def min_eig(eta):
+        Dg = np.concatenate([np.repeat(eta, np.diff(bp)), np.full(w.n, mu)])
+        return np.linalg.eigvalsh(np.diag(Dg) - sigma * A.T @ A).min()
+
+    eta = O.eta_blocks(Xt, bp, mu, 0.05, 1000, 1e-14)
+    lam = np.array([np.linalg.eigvalsh(Xt[:, bp[g]:bp[g + 1]].T @ Xt[:, bp[g]:bp[g + 1]]).max()
+                    for g in range(G)])
+    assert np.allclose(eta, 1.05 * mu * lam, rtol=1e-9)
+    assert min_eig(eta) >= -1e-12 * np.max(eta)
+    assert min_eig(mu * lam) >= -1e-12 * np.max(eta)   # the bound itself, with no margin
+    assert min_eig(0.5 * sigma * lam) < 0.0
