@@ -150,6 +150,111 @@ def make_workload():
 
 # ------------------------------------------------------------------ GB300 arm
 
+def fp64_plain_leg(ctx, step, B, mixed_iters, n_short, dev):
+    """Plain FP64 FS-QRPPA on the GPU, one fit at a time (the metric's comparison)."""
+    import torch
+
+    from paper_2601_02826_gb300 import fsqr, synth
+    from paper_2601_02826_gb300.device import upload
+    walls = []
+    for n_it in (n_short, 3 * n_short):
+        opts = dict(tol=0.0, max_iter=n_it, precision=fsqr.FP64, max_group=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(opts)
+        torch.cuda.synchronize()
+        walls.append(time.perf_counter() - t0)
+    s_per_iter = max(walls[1] - walls[0], 1e-9) / (B * 2 * n_short)
+    setup_s = max(walls[0] - B * n_short * s_per_iter, 0.0)
+    # iteration ratio FP64 / mixed on a small problem, both solved to the tolerance
+    w = synth.tiny_geno(7, 300, 500, c=2, fmt=synth.FMT_INT8, G=4, taus=(0.5,))
+    dw = upload(ctx, w, device=dev)
+    lam = 0.3 * ctx.lambda_max(dw.design, dw.y, 0.5, dw.omega)
+    its = {}
+    for prec in (fsqr.FP64, fsqr.MIXED):
+        b = torch.zeros(w.P, dtype=torch.float64, device=dev)
+        z = torch.zeros(w.n, dtype=torch.float64, device=dev)
+        th = torch.zeros(w.n, dtype=torch.float64, device=dev)
+        _, info = ctx.fit(dw.design, dw.y, 0.5, lam, dw.omega, w.block_ptr(), b, z, th,
+                          opts=dict(tol=TOL, max_iter=1_000_000, precision=prec))
+        its[prec] = info.iters
+    ratio = its[fsqr.FP64] / max(1, its[fsqr.MIXED])
+    need = float(np.mean(mixed_iters)) * ratio
+    step_s = setup_s + B * need * s_per_iter
+    return {"value": B / step_s, "unit": UNIT, "ms_per_iteration": s_per_iter * 1e3,
+            "setup_s_per_step": setup_s, "iterations_per_fit": need,
+            "iteration_ratio_fp64_over_mixed": ratio,
+            "sample": (f"{B} fits one at a time, timed at {n_short} and {3 * n_short} iterations each; "
+                       f"per-iteration time from the difference, set-up once per step; iterations = "
+                       f"mean mixed count x FP64/mixed ratio ({its[fsqr.FP64]}/{its[fsqr.MIXED]}) of a "
+                       f"300 x 500 fit solved to the tolerance in this run"),
+            "precision": "fp64", "max_group": 1}
+
+
+
+def grid_leg(ctx, dev, stream, iters, slots):
+    """The tau x lambda grid (9 tau x 20 lambda from lambda_max to 0.01
+    lambda_max = 180 fits; n = 10,000, p = 500,000 int8 genotypes, ragged
+    feature blocks U(5k, 30k)) solved as one wide batched solve: every fit
+    streams through `slots` slots sharing each X pass, and takes `iters`
+    steps of Algorithm 1 (tolerance 0; a throughput sample, since fits near
+    lambda_max need more than 3e5 steps to reach KKT <= 1e-6). Kernel times
+    come from a profiled 20-step run before the timed one."""
+    import torch
+
+    from paper_2601_02826_gb300 import fsqr, synth
+    from paper_2601_02826_gb300.device import upload
+    t0 = time.perf_counter()
+    w = synth.grid_int8()
+    t_gen = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        dw = upload(ctx, w, device=dev)
+    stream.synchronize()
+    taus = w.taus
+    fr = np.asarray(w.lambda_fracs)
+    lm = [ctx.lambda_max(dw.design, dw.y, t, dw.omega) for t in taus]
+    lam = np.array([[f * l for f in fr] for l in lm])
+    B = lam.size
+    beta = torch.zeros(B * w.P, dtype=torch.float64, device=dev)
+    z = torch.zeros(B * w.n, dtype=torch.float64, device=dev)
+    th = torch.zeros(B * w.n, dtype=torch.float64, device=dev)
+    opts = dict(tol=0.0, max_iter=iters, precision=fsqr.MIXED, max_group=slots)
+    ctx.profile(enable=True, reset=True)
+    ctx.fit_batch(dw.design, dw.y, taus, lam, dw.omega, w.block_ptr(), beta, z, th, opts=dict(opts, max_iter=20))
+    kp = ctx.profile(enable=False)
+    ctx.profile(reset=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc, infos = ctx.fit_batch(dw.design, dw.y, taus, lam, dw.omega, w.block_ptr(), beta, z, th, opts=opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    p = ctx.profile()
+    col_ms = kp.col_ms / max(1, kp.col_samples)
+    peak, kind = measured_peaks()
+    gbs = kp.col_bytes / (col_ms / 1e3) / 1e9
+    fit_its = sum(i.iters for i in infos)
+    setup_ms = float(np.mean([i.t_setup_ms for i in infos]))
+    solve_ms = ms - setup_ms
+    del dw, beta, z, th
+    torch.cuda.empty_cache()
+    return {"workload": "grid_int8", "n": w.n, "p": w.p, "G": len(w.block_sizes), "fits": B,
+            "slots": slots, "iterations_per_fit": iters, "steps": int(p.iterations), "ms": ms,
+            "setup_ms": setup_ms, "fit_iterations_per_s": fit_its / (solve_ms / 1e3),
+            "ms_per_step": solve_ms / max(1, p.iterations),
+            "col": {"kernel": f"k_wcol<{slots}> (X~^T Theta over all slots + beta prox)",
+                    "avg_launch_ms": col_ms, "bytes_per_launch": kp.col_bytes, "achieved_gbs": gbs,
+                    "peak_gbs": peak, "frac": gbs / peak, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({kind})"},
+            "xbeta_and_vector_update_ms": kp.xb_ms / max(1, kp.xb_samples),
+            "wide_groups": int(p.wide_groups), "gpu_launches": int(p.kernel_launches),
+            "generate_s": t_gen,
+            "note": "throughput sample: every fit takes the fixed number of steps (tolerance 0); "
+                    "setup (column statistics, 9 lambda_max, eta) inside ms"}
+
+
+
 def run_gb300(args, rank, world, local_rank):
     import torch
 
@@ -164,6 +269,7 @@ def run_gb300(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         dw = upload(ctx, w, device=dev)
     stream.synchronize()
+    gh_keep = None
     B = len(TAUS)
     bp = w.block_ptr()
     beta = torch.zeros(B * w.P, dtype=torch.float64, device=dev)
@@ -181,9 +287,18 @@ def run_gb300(args, rank, world, local_rank):
             infos_out.extend(infos)
         return rc
 
-    for _ in range(args.warmup):
+    # Kernel times come from events inside the solver, sampled during the last
+    # warm-up step only; the timed steps run with the sampling off.
+    for w_i in range(args.warmup):
+        if w_i == args.warmup - 1:
+            ctx.profile(enable=True, reset=True)
         step(mixed)
-    ctx.profile(enable=True, reset=True)
+    kprof = ctx.profile(enable=False)
+    if args.warmup == 0:  # no warm-up step to sample: take one extra, untimed
+        ctx.profile(enable=True, reset=True)
+        step(mixed)
+        kprof = ctx.profile(enable=False)
+    ctx.profile(enable=False, reset=True)
     infos = []
     dist = world > 1
     if dist:
@@ -203,14 +318,14 @@ def run_gb300(args, rank, world, local_rank):
     if dist:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
-    prof = ctx.profile(enable=False)
+    prof = ctx.profile()  # launches and iterations of the timed steps
     ms_max = max_over_ranks(ms, dev)
     fits = B * args.steps * world
     value = fits / (ms_max / 1e3)
 
     # roofline of the dominant kernel: the column pass (X~^T theta + prox)
-    col_avg_ms = prof.col_ms / max(1, prof.col_samples)
-    achieved = prof.col_bytes / (col_avg_ms / 1e3) / 1e9
+    col_avg_ms = kprof.col_ms / max(1, kprof.col_samples)
+    achieved = kprof.col_bytes / (col_avg_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     traffic = ncu_traffic(kernel_hash())
 
@@ -219,28 +334,13 @@ def run_gb300(args, rank, world, local_rank):
     kkts = [i.kkt for i in infos[-B:]]
 
     # plain FP64 GPU FS-QRPPA: one fit at a time, cold start (comparison).
-    # Timed on a bounded number of iterations per fit and scaled by the
-    # iterations the fits need (the same algorithm; FP64 products).
+    # Per-iteration time from two run lengths (their difference removes the
+    # set-up), the set-up added once per step, and FP64's own iteration count
+    # estimated as the mixed fits' count times the FP64/mixed iteration ratio
+    # of the same fits solved to the tolerance on a small problem in this run.
     fp64 = None
     if not args.skip_fp64 and rank == 0 and not args.profile_iters:
-        n_it = args.fp64_iters
-        fp_opts = dict(tol=0.0, max_iter=n_it, precision=fsqr.FP64, max_group=1)
-        ctx.profile(enable=True, reset=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        inf64 = []
-        step(fp_opts, inf64)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
-        p64 = ctx.profile(enable=False)
-        s_per_iter = t64 / (B * n_it)
-        need = float(np.mean(iters))
-        fp64 = {"value": 1.0 / (s_per_iter * need), "unit": UNIT,
-                "ms_per_iteration": s_per_iter * 1e3, "iterations_scaled_to": need,
-                "col_launch_ms": p64.col_ms / max(1, p64.col_samples),
-                "sample": f"{B} fits x {n_it} iterations timed (setup included), scaled to the "
-                          f"mean iteration count of the timed mixed fits",
-                "precision": "fp64", "max_group": 1}
+        fp64 = fp64_plain_leg(ctx, step, B, iters, args.fp64_iters, dev)
 
     # end to end through the host-buffer entry point (copies inside the call)
     e2e = None
@@ -260,7 +360,7 @@ def run_gb300(args, rank, world, local_rank):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        n_e2e = 1
+        n_e2e = max(1, min(args.steps, 3))
         for _ in range(n_e2e):
             ctx.fit_batch(dh, yh, TAUS, lam, oh, bp, bh, zh, thh, opts=mixed, host=True)
         torch.cuda.synchronize()
@@ -269,11 +369,18 @@ def run_gb300(args, rank, world, local_rank):
         d2h = 8 * (bh.numel() + zh.numel() + thh.numel())
         e2e = {"value": B * n_e2e * world / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h),
+               "steps": n_e2e,
                "note": "fsqr_fit_batch_host from pinned host buffers; lambda from a device call"}
 
     cpu = None
     if rank == 0 and not args.skip_cpu and not args.profile_iters:
         cpu = cpu_baseline(w, iters)
+
+    grid = None
+    if not args.skip_grid and not args.profile_iters:
+        del dw, gh_keep
+        torch.cuda.empty_cache()
+        grid = grid_leg(ctx, dev, stream, args.grid_iters, args.grid_slots)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -289,17 +396,18 @@ def run_gb300(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_col_tc (column pass: X~^T theta on tcgen05 + beta prox)",
-                     "bytes_per_launch": prof.col_bytes, "avg_launch_ms": col_avg_ms,
-                     "samples": prof.col_samples, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+                     "bytes_per_launch": kprof.col_bytes, "avg_launch_ms": col_avg_ms,
+                     "samples": kprof.col_samples, "sampled_in": "last warm-up step (timed steps unsampled)", "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
         "kernels_ms": {"col": col_avg_ms,
-                       "xbeta_and_vector_update": prof.xb_ms / max(1, prof.xb_samples),
-                       "vec": (prof.vec_ms / prof.vec_samples) if prof.vec_samples else None},
+                       "xbeta_and_vector_update": kprof.xb_ms / max(1, kprof.xb_samples),
+                       "vec": (kprof.vec_ms / kprof.vec_samples) if kprof.vec_samples else None},
         "iters": iters, "kkt": kkts, "iterations_timed": prof.iterations,
         "gpu_launches": int(prof.kernel_launches),
         "clocks": clocks.summary(),
         "e2e": e2e,
         "fp64_plain": fp64,
         "cpu_baseline": cpu,
+        "grid": grid,
         "wall_s": t_wall,
     }
     if fp64:
@@ -347,12 +455,31 @@ class OracleSample:
 
 
 def cpu_baseline(w, iters_needed, sample_iters=40):
-    """The FP64 oracle timed on the host on a bounded sample, scaled to fits/s."""
+    """The FP64 oracle timed on the host on a bounded sample, scaled to fits/s:
+    with the BLAS default threads (all host cores) and, in a child process
+    with every BLAS pool set to one thread, single-threaded."""
     o = OracleSample(w)
     spi = o.seconds_per_iteration(sample_iters)
     mean_iters = float(np.mean(iters_needed))
+    single = oracle_single_thread(sample_iters // 2, mean_iters)
     return {"value": 1.0 / (spi * mean_iters), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": o.describe(sample_iters, spi, mean_iters)}
+            "sample": o.describe(sample_iters, spi, mean_iters), "single_thread": single}
+
+
+def oracle_single_thread(sample_iters, mean_iters):
+    """Seconds per oracle iteration with one BLAS thread (child process)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "o = bench.OracleSample(bench.make_workload()); "
+            "print(json.dumps(o.seconds_per_iteration(%d)))" % (ROOT, sample_iters))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+        spi = float(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+    return {"value": 1.0 / (spi * mean_iters), "unit": UNIT, "cores": 1, "ms_per_iteration": spi * 1e3,
+            "sample": f"{sample_iters} iterations of the tau=0.5 fit, one BLAS thread"}
 
 
 def run_reference(args, rank, world):
@@ -454,6 +581,10 @@ def main():
     # (144110, 182730, 146700 for tau = 0.1, 0.5, 0.9; same algorithm)
     ap.add_argument("--ref-iters", type=int, default=157847)
     ap.add_argument("--fp64-iters", type=int, default=400)
+    ap.add_argument("--skip-grid", action="store_true")
+    ap.add_argument("--grid-iters", type=int, default=500,
+                    help="iterations per fit of the tau x lambda grid leg (a throughput sample)")
+    ap.add_argument("--grid-slots", type=int, default=32)
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: every fit stops after this many iterations (not a bench line)")
     ap.add_argument("--grid-sample", action="store_true",

@@ -124,14 +124,38 @@ typedef struct {
   int32_t digits;         /* FSQR_MIXED_SIMT: int8 (7-bit) digits per theta entry, 3..5;
                              FSQR_MIXED uses 7 base-16 digits (6 when digits == 3);
                              default 4 */
-  int32_t max_group;      /* fits advanced together per X pass, 1..8, or 0: chosen by
-                             timing the candidates 1, 2, 3, 4 and min(B, 8) on the
-                             first fits (a short cold run of each, cached per context
-                             and problem shape; fsqr_profile.tuned_group reports it);
-                             default 4 */
+  int32_t max_group;      /* fits advanced together per X pass, 1..32, or 0: chosen by
+                             timing the candidates 1, 2, 3, 4, min(B, 8) and, on the
+                             tensor-core path with B > 8 fits, 16 and 32 on the first
+                             fits (a short cold run of each, cached per context, problem
+                             shape and block partition; fsqr_profile.tuned_group reports
+                             it); default 4. Above 8, on the tensor-core path only
+                             (FSQR_MIXED, int8 storage), the fits of fsqr_fit_batch stream
+                             through 16 (max_group <= 16) or 32 slots of one solve: a
+                             slot whose fit has stopped takes the next fit (with
+                             FSQR_WARM_PATH, the next fit of a tau's path starts from
+                             its predecessor's solution as soon as that one stops).
+                             Elsewhere values above 8 act as 8. */
   int64_t timeout_ms;     /* > 0: stop with FSQR_ETIMEOUT after this wall time */
   const float *warm_params; /* device, fsqr_mlp_param_count() floats: the network of
                                FSQR_WARM_LEARNED; default NULL */
+  double ridge;           /* gamma >= 0: weighted elastic net (Section 5, closing remark),
+                             Omega(beta) = sum_j lambda_j |beta_j| + (gamma/2) sum_j omega_j beta_j^2;
+                             the beta step divides the soft threshold by eta_g + gamma omega_j,
+                             R_b measures dist(s_j - gamma omega_j beta_j, lambda_j d|beta_j|),
+                             info.primal includes the quadratic term and info.gap is NaN
+                             when gamma > 0; default 0 (the weighted-l1 penalty) */
+  int32_t screen;         /* 1 (fsqr_fit_batch with FSQR_WARM_PATH, at most 8 taus): the
+                             sequential strong rule along each tau's path. At stage l a stored
+                             column j is left out of the stage's fits when, for every tau,
+                             beta_j = 0 at lambda_{l-1} and |x~_j^T theta| < omega_j (2 lambda_l -
+                             lambda_{l-1}) there (at l = 0 the lambda_max direction, with
+                             lambda_{-1} = lambda_max); the fits run on the kept columns only, and
+                             every left-out column is then checked on the full design: one with
+                             (|x~_j^T theta| - lambda_j)_+ / lambda_max > tol is put back and the
+                             stage re-solved, so returned fits meet the stop test on all columns.
+                             fsqr_profile.screen_kept/screen_total count the columns streamed.
+                             default 0 */
 } fsqr_opts;
 
 /* Per-fit report. */
@@ -207,6 +231,28 @@ int fsqr_fit_batch(fsqr_ctx *ctx, const fsqr_design *X, const double *y, int n_t
                    const int64_t *block_ptr, int G, const fsqr_opts *opts, double *beta,
                    double *z, double *theta, fsqr_info *infos);
 
+/* ---- folded-concave penalties (Section 6, Algorithm 2) ------------------ */
+#define FSQR_PEN_SCAD 1 /* p' of eq. scad: lambda (t <= lambda), (a lambda - t)/(a - 1)
+                           (lambda < t < a lambda), 0 (t >= a lambda); a > 2 */
+#define FSQR_PEN_MCP 2  /* p' of eq. mcp: lambda - t/a (t <= a lambda), 0 beyond; a > 1 */
+
+/* L-step local linear approximation (LLA) for SCAD or MCP (Algorithm 2):
+ * the weighted-l1 fit at lambda_j = lambda omega_j (as fsqr_fit), then L
+ * fits with lambda_j = omega_j p'_lambda(|beta~_j|) from the previous fit's
+ * beta~ (standardised scale), each started from the previous (beta, z,
+ * theta) with the same eta_g. The paper uses L = 1, a = 3.7 (SCAD), a = 3
+ * (MCP). R_b of every step is divided by lambda_max(tau) of omega.
+ *   lambda > 0; omega as for fsqr_fit (its zeros stay unpenalised).
+ *   beta, z, theta: device, in/out as for fsqr_fit (opts.warm applies to
+ *   the first fit); on return the last step's iterate.
+ *   lam_out: device, length P, or NULL: the last step's lambda_j.
+ *   info: the last step's report, with iters = the steps of all L + 1 fits.
+ * Returns the last fit's status (FSQR_OK, FSQR_ENOCONV, FSQR_ETIMEOUT). */
+int fsqr_fit_lla(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau, double lambda,
+                 const double *omega, const int64_t *block_ptr, int G, int penalty, double a, int L,
+                 const fsqr_opts *opts, double *beta, double *z, double *theta, double *lam_out,
+                 fsqr_info *info);
+
 /* fsqr_fit_batch from HOST buffers: X->geno, X->cov, X->col_mean/col_sd, y,
  * omega, beta, z, theta are host pointers. The library copies the inputs to
  * device workspace, solves, and copies beta/z/theta back; the copies are
@@ -231,6 +277,29 @@ int fsqr_kkt(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau, d
  * in X so that they are standardised the same way. out: device, B*n. */
 int fsqr_predict(fsqr_ctx *ctx, const fsqr_design *X, const double *beta, int B, double *out);
 
+/* Model selection along a lambda path (Section 7). For B fits (beta: device,
+ * B*P, standardised scale; taus: host, B quantile levels) evaluated on the
+ * design X with response y (device, n): the training data for HBIC, or a
+ * validation set (its col_mean/col_sd set to the training ones) for the
+ * validation loss. Host outputs of B entries, each may be NULL:
+ *   loss[b]   = (1/n) sum_i rho_tau_b(y_i - x~_i^T beta_b)
+ *   active[b] = #{j >= 1 : beta_b,j != 0}
+ *   hbic[b]   = log(sum_i rho_tau_b(y_i - x~_i^T beta_b))
+ *               + active[b] (log log n / n) log(P - 1)   (C_n = log p)
+ * The paper picks the lambda of least HBIC in sparse settings and of least
+ * validation loss in dense ones. */
+int fsqr_path_stats(fsqr_ctx *ctx, const fsqr_design *X, const double *y, int B, const double *taus,
+                    const double *beta, double *loss, int64_t *active, double *hbic);
+
+/* Prediction intervals [q_lo(x), q_hi(x)] = [x~^T beta_lo, x~^T beta_hi]
+ * (Section 7.1, e.g. the fits at tau = 0.1 and 0.9) on the samples of X,
+ * y (device). Host outputs, each may be NULL: coverage = fraction of samples
+ * with q_lo <= y <= q_hi whose interval does not cross (q_lo <= q_hi; a
+ * crossing counts as a miss); width = mean of q_hi - q_lo; crossings =
+ * number of samples with q_lo > q_hi. */
+int fsqr_interval_coverage(fsqr_ctx *ctx, const fsqr_design *X, const double *y, const double *beta_lo,
+                           const double *beta_hi, double *coverage, double *width, int64_t *crossings);
+
 /* Maps B standardised coefficient vectors to the original feature scale
  * (Section 7): b_j / sd_j for j >= 1 (0 for a constant column) and
  * b_0 - sum_j mean_j b_j / sd_j. beta_std, beta_out: device, B*P. */
@@ -254,9 +323,27 @@ typedef struct {
   int64_t kernel_launches;
   int64_t col_bytes;                     /* algorithmic bytes of the last column pass */
   int64_t tuned_group;                   /* group size the autotuner chose last (0: none) */
+  int64_t tc_groups;                     /* groups of <= 8 fits solved on the tensor-core passes */
+  int64_t simt_groups;                   /* groups solved on the SIMT passes (FP64, FSQR_MIXED_SIMT,
+                                            2-bit storage, or sizes beyond the tensor-core bounds) */
+  int64_t wide_groups;                   /* wide solves (16 or 32 slots, tensor cores) */
+  int64_t screen_kept, screen_total;     /* screened path solves: stored columns kept / all, summed
+                                            over stages, rounds and quantiles */
 } fsqr_profile;
 
 int fsqr_profile_enable(fsqr_ctx *ctx, int on);
+
+/* Self-test of the device-side failure detection (no counterpart in the
+ * paper). Every wait inside the pipelined kernels gives up after a cycle
+ * budget (about one second), records a code in a device error word and
+ * returns, so that a stalled pipeline ends the call with an error instead of
+ * hanging the GPU. This entry point runs that wait in isolation: one CTA
+ * waits on a barrier with a budget of budget_cycles (0..4e9); with arrive = 0
+ * nothing ever arrives on it, with arrive = 1 its one arrival comes first.
+ * wait_ok (host, may be NULL) receives 1 if the wait succeeded. Returns
+ * FSQR_ETIMEOUT when the wait ran out (the context stays usable), FSQR_OK
+ * when it succeeded. */
+int fsqr_wait_selftest(fsqr_ctx *ctx, int64_t budget_cycles, int arrive, int *wait_ok);
 int fsqr_profile_get(fsqr_ctx *ctx, fsqr_profile *out);
 int fsqr_profile_reset(fsqr_ctx *ctx);
 

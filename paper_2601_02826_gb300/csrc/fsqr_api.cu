@@ -171,7 +171,7 @@ int check_blocks(fsqr_ctx *ctx, const int64_t *bp, int G, int64_t P) {
 // Design prepared for the kernels: affine maps a_j, b_j from the column
 // statistics (given or computed), and the count of missing entries.
 struct Prep {
-  Dsg X;
+  Dsg X{};
   const double *mean = nullptr;  // length c+p
   const double *sd = nullptr;
   int missing = 0;
@@ -190,6 +190,8 @@ int prepare(fsqr_ctx *ctx, const fsqr_design *d, Prep *pp, bool need_colbound) {
   X.geno = static_cast<const uint8_t *>(d->geno);
   X.ld = d->geno_ld;
   X.cov = d->cov;
+  X.mptr = nullptr;
+  X.midx = nullptr;
   const int64_t F = d->c + d->p;
   double *mean, *sd, *a, *b;
   int *miss;
@@ -215,11 +217,46 @@ int prepare(fsqr_ctx *ctx, const fsqr_design *d, Prep *pp, bool need_colbound) {
   }
   CK(cudaStreamSynchronize(ctx->stream));
   p.missing = hmiss;
-  if (hmiss > 0)
-    return fail(ctx, FSQR_EINVAL,
-                "%d missing genotype entries: mean imputation of missing entries is not "
-                "supported by this library",
-                hmiss);
+  if (X.c > 0 || X.fmt == FSQR_DENSE_F64) {
+    // non-finite dense values make the column statistics non-finite
+    double *st3;
+    TRY(wsget(ctx, "stat_chk", 3, &st3));
+    LK(launch_vec_stats(mean, F, st3, ctx->stream));
+    double h[3];
+    CK(cudaMemcpyAsync(h, st3, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!std::isfinite(h[0]) || !std::isfinite(h[2]))
+      return fail(ctx, FSQR_ENUMERIC, "a covariate or dense feature column contains NaN or Inf");
+  }
+  if (hmiss > 0) {
+    // mean imputation (Section 7.2): per stored column the ascending list of
+    // its missing samples; int8 codes are read from a copy whose missing
+    // codes are 0 (the E4M3 reading of the tensor-core passes needs 0/1/2)
+    const int64_t pc = X.p;
+    int *cnt;
+    int64_t *mptr;
+    TRY(wsget(ctx, "miss_cnt", (size_t)pc, &cnt));
+    TRY(wsget(ctx, "miss_ptr", (size_t)pc + 1, &mptr));
+    LK(launch_miss_count(X, cnt, ctx->stream));
+    std::vector<int> hc((size_t)pc);
+    std::vector<int64_t> hp((size_t)pc + 1, 0);
+    CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * pc, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int64_t q = 0; q < pc; ++q) hp[q + 1] = hp[q] + hc[q];
+    int32_t *midx;
+    TRY(wsget(ctx, "miss_idx", (size_t)std::max<int64_t>(hp[pc], 1), &midx));
+    CK(cudaMemcpyAsync(mptr, hp.data(), sizeof(int64_t) * (pc + 1), cudaMemcpyHostToDevice, ctx->stream));
+    LK(launch_miss_fill(X, mptr, midx, ctx->stream));
+    if (X.fmt == FSQR_INT8) {
+      uint8_t *clean;
+      TRY(wsget(ctx, "miss_geno", (size_t)(pc * X.ld), &clean));
+      LK(launch_sanitize_int8(X, clean, ctx->stream));
+      X.geno = clean;
+    }
+    X.mptr = mptr;
+    X.midx = midx;
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
   return FSQR_OK;
 }
 
@@ -363,6 +400,7 @@ int eta_impl(fsqr_ctx *ctx, const Prep &pr, const int64_t *bp, int G, double mu,
   int left = G;
   for (int t = 1; t <= max_iter && left > 0; ++t) {
     LK(launch_xv_blocks(X, v, d_splits, d_sob, G, nsplit, U, npad, part, ctx->stream));
+    if (X.mptr) LK(launch_miss_xv(X, v, d_bp, G, U, npad, ctx->stream));
     LK(launch_sum_cols(U, n, npad, G, usum, usq, ctx->stream));
     LK(launch_col_pass(A_XT_BLOCK, 1, X, F, 0, U, usum, w, nullptr, ctx->stream));
     LK(launch_power_step(w, d_bp, G, P, v, wn, ctx->stream));
@@ -404,13 +442,15 @@ int check_opts(fsqr_ctx *ctx, const fsqr_opts *o, int G) {
     return fail(ctx, FSQR_EINVAL, "FSQR_WARM_LEARNED needs opts.warm_params");
   if (o->precision != FSQR_FP64 && (o->digits < 3 || o->digits > 5))
     return fail(ctx, FSQR_EINVAL, "digits must be in 3..5");
-  if (o->max_group < 0 || o->max_group > kMaxNB)
-    return fail(ctx, FSQR_EINVAL, "max_group must be in 0..8");
+  if (o->max_group < 0 || o->max_group > kWideMax)
+    return fail(ctx, FSQR_EINVAL, "max_group must be in 0..32");
   if (o->eta)
     for (int g = 0; g < G; ++g)
       if (!(o->eta[g] > 0.0) || isinf(o->eta[g]))
         return fail(ctx, FSQR_EINVAL, "eta[%d] must be finite and > 0", g);
   if (!(o->eta_margin >= 0.0)) return fail(ctx, FSQR_EINVAL, "eta_margin must be >= 0");
+  if (!(o->ridge >= 0.0) || isinf(o->ridge)) return fail(ctx, FSQR_EINVAL, "ridge must be finite and >= 0");
+  if (o->screen != 0 && o->screen != 1) return fail(ctx, FSQR_EINVAL, "screen must be 0 or 1");
   return FSQR_OK;
 }
 
@@ -437,20 +477,24 @@ struct SolveEnv {
   double deadline_ms;        // <= 0: none
 };
 
+// The tensor-core passes run for int8 storage with at most 63 covariates and
+// sizes for which the integer arithmetic stays exact: a digit-product sum
+// over n samples (or over the active columns of an X~ beta split, at most
+// p) of |g t| <= 16 is a multiple of 2^-9 below 2^24 * 2^-9 in FP32 when
+// n, p <= 2^20; the recombined X~ beta, sum_j g_ij W_j with |W_j| < 2^43,
+// stays below 2^63 in int64 when p <= 2^19.
+bool tc_eligible(const Dsg &X, int precision) {
+  return precision == FSQR_MIXED && X.fmt == FSQR_INT8 && X.p > 0 && X.c <= 63 && X.n <= ((int64_t)1 << 20) &&
+         X.p <= ((int64_t)1 << 19);
+}
+
 int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   const Dsg &X = E.pr->X;
   const int nb = gs.nb;
   const int NB = nb_template(nb);
   const int64_t n = X.n, npad = pad16(n), P = X.P;
   const bool mixed = E.o->precision == FSQR_MIXED || E.o->precision == FSQR_MIXED_SIMT;
-  // tensor-core passes: int8 storage, at most 63 covariates, <= 8 fits, and
-  // sizes for which the integer arithmetic stays exact: a digit-product sum
-  // over n samples (or over the active columns of an X~ beta split, at most
-  // p) of |g t| <= 16 is a multiple of 2^-9 below 2^24 * 2^-9 in FP32 when
-  // n, p <= 2^20; the recombined X~ beta, sum_j g_ij W_j with |W_j| < 2^43,
-  // stays below 2^63 in int64 when p <= 2^19
-  const bool tc = E.o->precision == FSQR_MIXED && X.fmt == FSQR_INT8 && X.p > 0 && X.c <= 63 && NB <= 8 &&
-                  X.n <= ((int64_t)1 << 20) && X.p <= ((int64_t)1 << 19);
+  const bool tc = tc_eligible(X, E.o->precision) && NB <= 8;
   const double t0 = now_ms();
   cudaStream_t st = ctx->stream;
 
@@ -473,6 +517,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   F.mu = E.mu;
   F.sigma = E.mu / (double)(E.G + 1);
   F.tol = E.o->tol;
+  F.ridge = E.o->ridge;
   F.K = E.o->check_every;
   F.max_iter = E.o->max_iter;
   F.mixed = mixed ? 1 : 0;
@@ -556,6 +601,10 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     TRY(wsget(ctx, "g_xbipart", (size_t)kBMaxSplits * npad * NB, &F.xb_ipart));
     TRY(wsget(ctx, "g_awmax", (size_t)F.gridA * NB, &F.a_wmax));
   }
+  if (X.mptr) {
+    TRY(wsget(ctx, "g_qcorr", (size_t)npad * NB, &F.qcorr));
+    CK(cudaMemsetAsync(F.qcorr, 0, sizeof(double) * npad * NB, st));
+  }
   if (!tc) {
     const size_t smem = col_pass_smem(A_PROX, F, NB);
     if (smem > 227 * 1024)
@@ -588,6 +637,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   LK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, F.beta[0], st));
   if (tc) LK(launch_xbeta_tc(NB, X, F, 0, 0, F.beta[0], scol, wtile, d_err, ctx->num_sms, st));
   else LK(launch_xbeta(NB, X, F, 0, F.beta[0], st));
+  if (F.qcorr) LK(launch_miss_xb(NB, X, F, 0, F.beta[0], st));
   LK(launch_vec(NB, X, F, 0, 1, st));
 
   // ---- the iteration as a captured graph of M steps
@@ -598,7 +648,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     for (int e = 0; e < 6; ++e) CK(cudaEventCreate(&ctx->ev[e]));
   // kernels per step: [quantize] col [check] (xprep + fused xbeta/vector | xbeta + vec)
   int per_graph = 1;  // the advance kernel
-  for (int off = 0; off < M; ++off) per_graph += (mixed ? 1 : 0) + 3 + (off % K == 0 ? 1 : 0);
+  for (int off = 0; off < M; ++off) per_graph += (mixed ? 1 : 0) + 3 + (off % K == 0 ? 1 : 0) + (F.qcorr ? 1 : 0);
   // Enqueues steps base..base+M-1 (kernels read the base from it_base); with
   // sample set, events bracket the kernels of the last step. The stop test of
   // w^k reads only the column pass of step k and the vector pass of step k-1,
@@ -618,6 +668,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
       }
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[1], st);
       if (off % K == 0 && ce == cudaSuccess) ce = launch_check(NB, F, off, st);
+      if (F.qcorr && ce == cudaSuccess) ce = launch_miss_xb(NB, X, F, off, nullptr, st);
       if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], st);
       if (ce == cudaSuccess)
         ce = tc ? launch_xbeta_tc(NB, X, F, off, 1, nullptr, scol, wtile, d_err, ctx->num_sms, st)
@@ -692,6 +743,8 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
   }
   cudaGraphExecDestroy(exec);
   if (rc != FSQR_OK) return rc;
+  if (tc) ctx->pf.tc_groups += 1;
+  else ctx->pf.simt_groups += 1;
   if (tc) {
     int herr = 0;
     CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -751,7 +804,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
       schk_use = schk;
       tc_use = tc;
     }
-    LK(launch_summary(NB, nb, n, P, E.y, F.z, F.r, bfin, E.omega, dtaus, dlams, schk_use, tc_use,
+    LK(launch_summary(NB, nb, n, P, E.y, F.z, F.r, bfin, E.omega, dtaus, dlams, schk_use, tc_use, E.o->ridge,
                       summ, st));
     double hs[kMaxNB * 8];
     CK(cudaMemcpyAsync(hs, summ, sizeof(double) * kMaxNB * 8, cudaMemcpyDeviceToHost, st));
@@ -790,6 +843,428 @@ int warm_start_impl(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, 
                     const double *omega, const float *params, double ysd, double *beta, double *z,
                     double *theta);
 
+int predict_impl(fsqr_ctx *ctx, const Prep &pr, const double *beta, int B, double *out);
+
+// One fit of a wide solve: its parameters, where its result goes and how it
+// starts (cold, from the user's arrays, or from another fit's solution).
+struct WideFit {
+  double tau, lam, lamnorm;
+  int fit;   // output index
+  int from;  // -1 cold; >= 0 start from that fit's result (it must finish first)
+  bool given;  // start from the user's arrays of this fit (FSQR_WARM_GIVEN / LEARNED)
+};
+
+// Wide slot scheduler (batched tau x lambda grid, tensor-core path): NB = 16
+// or 32 slots share every X pass. The iteration runs as a captured CUDA
+// graph of M steps; between replays the host reads the per-slot done flags,
+// moves each finished fit's iterate to the user's arrays, and refills the
+// slot with the next ready fit (a fit whose start is another fit's solution
+// becomes ready when that fit finishes). Each fit keeps its own iteration
+// count from the step at which it entered its slot, so the iterates of a fit
+// are those of Algorithm 1 run alone; idle slots carry zero digits.
+int solve_wide(fsqr_ctx *ctx, const SolveEnv &E, int NB, const std::vector<WideFit> &fits) {
+  const Dsg &X = E.pr->X;
+  const int64_t n = X.n, npad = pad16(n), P = X.P;
+  const int nf = (int)fits.size();
+  cudaStream_t st = ctx->stream;
+  const double t0 = now_ms();
+
+  Fits F{};
+  F.nb = NB;
+  F.n = n;
+  F.npad = npad;
+  F.y = E.y;
+  F.ymax = E.ymax;
+  F.omega = E.omega;
+  F.block_ptr = E.d_bp;
+  F.G = E.G;
+  F.eta = E.d_eta;
+  F.inv_eta = E.d_ieta;
+  for (int b = 0; b < kMaxNB; ++b) { F.tau[b] = 0.5; F.lam[b] = 0.0; F.lamnorm[b] = 1.0; }
+  F.mu = E.mu;
+  F.sigma = E.mu / (double)(E.G + 1);
+  F.tol = E.o->tol;
+  F.ridge = E.o->ridge;
+  F.K = E.o->check_every;
+  F.max_iter = E.o->max_iter;
+  F.mixed = 1;
+  F.D = 7;
+  F.dbits = 4;
+  F.DW = 11;
+  F.th_unit = ldexp(1.0, -28);
+  F.xb_unit = ldexp(1.0, -44);
+  F.n4p = npad / 4;
+  F.colbound = E.pr->colbound;
+  TcSchedule tsc{};
+  col_tc_schedule(X.p, n, ctx->num_sms, &tsc);
+  tsc.slices = 0;
+  tsc.slots = tsc.grid;
+  F.T = tsc.list_stride;
+  F.gridA = tsc.grid;
+  const int rows = (int)((n + 127) / 128);
+  F.gridC = rows;
+  if (wcol_smem(NB, F.T) > 227 * 1024)
+    return fail(ctx, FSQR_EINVAL, "wide column pass needs %zu B of shared memory", wcol_smem(NB, F.T));
+  TRY(wsget(ctx, "w_beta0", (size_t)P * NB, &F.beta[0]));
+  TRY(wsget(ctx, "w_beta1", (size_t)P * NB, &F.beta[1]));
+  TRY(wsget(ctx, "w_z", (size_t)npad * NB, &F.z));
+  TRY(wsget(ctx, "w_theta", (size_t)npad * NB, &F.theta));
+  TRY(wsget(ctx, "w_r", (size_t)npad * NB, &F.r));
+  TRY(wsget(ctx, "w_arb", (size_t)F.gridA * NB, &F.a_rb));
+  TRY(wsget(ctx, "w_act", (size_t)F.gridA * NB, &F.a_ct));
+  TRY(wsget(ctx, "w_awmax", (size_t)F.gridA * NB, &F.a_wmax));
+  TRY(wsget(ctx, "w_acnt", (size_t)F.gridA, &F.a_cnt));
+  TRY(wsget(ctx, "w_alist", (size_t)F.gridA * F.T, &F.a_list));
+  TRY(wsget(ctx, "w_metai", 4, &F.meta_i));
+  TRY(wsget(ctx, "w_metad", 2 * kWideMax, &F.meta_d));
+  TRY(wsget(ctx, "w_cpart0", (size_t)rows * NB * kCPartials, &F.c_part[0]));
+  TRY(wsget(ctx, "w_cpart1", (size_t)rows * NB * kCPartials, &F.c_part[1]));
+  TRY(wsget(ctx, "w_totc0", (size_t)kWideMax * kCPartials, &F.tot_c[0]));
+  TRY(wsget(ctx, "w_totc1", (size_t)kWideMax * kCPartials, &F.tot_c[1]));
+  TRY(wsget(ctx, "w_tota", (size_t)kWideMax * 3, &F.tot_a));
+  TRY(wsget(ctx, "w_apre", (size_t)F.gridA + 1, &F.a_pre));
+  TRY(wsget(ctx, "w_tick", 2, &F.tickets));
+  TRY(wsget(ctx, "w_xbtick", (size_t)rows, &F.xb_tick));
+  TRY(wsget(ctx, "w_done", kWideMax, &F.done));
+  TRY(wsget(ctx, "w_ndone", 1, &F.n_done));
+  TRY(wsget(ctx, "w_report", (size_t)kWideMax * kReport, &F.report));
+  TRY(wsget(ctx, "w_scale", kWideMax, &F.scale));
+  TRY(wsget(ctx, "w_xbipart", (size_t)16 * npad * NB, &F.xb_ipart));
+  int *it_base;
+  TRY(wsget(ctx, "w_itbase", 1, &it_base));
+  F.it_base = it_base;
+  double *d_tau, *d_lam, *d_lamnorm, *zero, *rfit;
+  int *d_k0, *d_mask, *d_err, *scol;
+  TRY(wsget(ctx, "w_tau", kWideMax, &d_tau));
+  TRY(wsget(ctx, "w_lam", kWideMax, &d_lam));
+  TRY(wsget(ctx, "w_lamnorm", kWideMax, &d_lamnorm));
+  TRY(wsget(ctx, "w_k0", kWideMax, &d_k0));
+  TRY(wsget(ctx, "w_mask", kWideMax, &d_mask));
+  TRY(wsget(ctx, "w_zero", (size_t)std::max<int64_t>(P, npad), &zero));
+  TRY(wsget(ctx, "w_rfit", (size_t)nf * n, &rfit));
+  TRY(wsget(ctx, "g_err", 1, &d_err));
+  F.w_tau = d_tau;
+  F.w_lam = d_lam;
+  F.w_lamnorm = d_lamnorm;
+  F.w_k0 = d_k0;
+  const int64_t nk = (n + 127) / 128, ntile = (X.p + 127) / 128, maxkb = (P + 127) / 128;
+  uint8_t *dg, *xt, *wtile;
+  TRY(wsget(ctx, "w_dg", (size_t)(nk * wide_rows(NB) * 128), &dg));
+  TRY(wsget(ctx, "g_xt", (size_t)(ntile * nk * 16384), &xt));
+  TRY(wsget(ctx, "g_scol", (size_t)(maxkb * 128), &scol));
+  TRY(wsget(ctx, "w_wtile", (size_t)(maxkb * wide_xrows(NB) * 128), &wtile));
+  double *xbtmp;
+  TRY(wsget(ctx, "w_xbtmp", (size_t)npad, &xbtmp));
+  if (X.mptr) {
+    TRY(wsget(ctx, "w_qcorr", (size_t)npad * NB, &F.qcorr));
+    CK(cudaMemsetAsync(F.qcorr, 0, sizeof(double) * npad * NB, st));
+  }
+  CK(cudaMemsetAsync(dg, 0, (size_t)(nk * wide_rows(NB) * 128), st));
+  CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(zero, 0, sizeof(double) * std::max<int64_t>(P, npad), st));
+  CK(cudaMemsetAsync(F.xb_tick, 0, sizeof(unsigned) * rows, st));
+  CK(cudaMemsetAsync(F.tickets, 0, 2 * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(F.tot_c[0], 0, sizeof(double) * kWideMax * kCPartials, st));
+  CK(cudaMemsetAsync(F.tot_c[1], 0, sizeof(double) * kWideMax * kCPartials, st));
+  CK(cudaMemsetAsync(F.tot_a, 0, sizeof(double) * kWideMax * 3, st));
+  CK(cudaMemsetAsync(F.report, 0, sizeof(double) * kWideMax * kReport, st));
+  CK(cudaMemsetAsync(F.beta[0], 0, sizeof(double) * P * NB, st));
+  CK(cudaMemsetAsync(F.beta[1], 0, sizeof(double) * P * NB, st));
+  CK(cudaMemsetAsync(F.z, 0, sizeof(double) * npad * NB, st));
+  CK(cudaMemsetAsync(F.theta, 0, sizeof(double) * npad * NB, st));
+  CK(cudaMemsetAsync(F.r, 0, sizeof(double) * npad * NB, st));
+  CK(cudaMemsetAsync(it_base, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(F.n_done, 0, sizeof(int), st));
+  LK(launch_tile_x(X, xt, nk, st));
+
+  // host mirror of the per-slot state (pinned: done flags and reports come back every replay)
+  double *hp;
+  TRY(pinned(ctx, (size_t)kWideMax * kReport + 4 * kWideMax + 64, &hp));
+  double *hrep = hp;
+  int *hdone = reinterpret_cast<int *>(hp + kWideMax * kReport);
+  std::vector<int> slot_fit(NB, -1), hk0(NB, 0), hmask(NB, 0);
+  std::vector<double> htau(NB, 0.5), hlam(NB, 0.0), hlamn(NB, 1.0);
+  std::vector<int> state(nf, 0);  // 0 waiting, 1 running, 2 finished
+  std::vector<int> fit_pos(nf, 0);
+  for (int q = 0; q < nf; ++q) fit_pos[q] = q;
+  std::vector<int> pos_of_fit;  // output fit index -> position in fits
+  {
+    int mx = 0;
+    for (const WideFit &w : fits) mx = std::max(mx, w.fit);
+    pos_of_fit.assign(mx + 1, -1);
+    for (int q = 0; q < nf; ++q) pos_of_fit[fits[q].fit] = q;
+  }
+  const int kIdle = 0x7fffffff;
+  for (int b = 0; b < NB; ++b) hdone[b] = kIdle;
+  int next = 0, finished = 0;
+  int host_base = 0;
+  bool timed_out = false;
+
+  // fills the empty slots with ready fits at iteration host_base
+  auto fill = [&]() -> int {
+    const int par = host_base & 1;
+    bool any = false;
+    for (int b = 0; b < NB; ++b) {
+      if (slot_fit[b] >= 0) continue;
+      int pick = -1;
+      for (int q = next; q < nf; ++q) {
+        if (state[q] != 0) continue;
+        const int src = fits[q].from;
+        if (src >= 0 && (src >= (int)pos_of_fit.size() || pos_of_fit[src] < 0 || state[pos_of_fit[src]] != 2))
+          continue;
+        pick = q;
+        break;
+      }
+      if (pick < 0) break;
+      const WideFit &w = fits[pick];
+      state[pick] = 1;
+      while (next < nf && state[next] != 0) ++next;
+      slot_fit[b] = pick;
+      double *bs = F.beta[par] + b, *zs = F.z + b, *ts = F.theta + b, *rs = F.r + b;
+      if (w.from >= 0) {
+        const int sf = w.from;
+        LK(launch_pack(E.beta + (int64_t)sf * P, P, bs, P, 1, NB, P, st));
+        LK(launch_pack(E.z + (int64_t)sf * n, n, zs, n, 1, NB, npad, st));
+        LK(launch_pack(E.theta + (int64_t)sf * n, n, ts, n, 1, NB, npad, st));
+        LK(launch_pack(rfit + (int64_t)pos_of_fit[sf] * n, n, rs, n, 1, NB, npad, st));
+      } else if (w.given) {
+        const int f = w.fit;
+        LK(launch_pack(E.beta + (int64_t)f * P, P, bs, P, 1, NB, P, st));
+        LK(launch_pack(E.z + (int64_t)f * n, n, zs, n, 1, NB, npad, st));
+        LK(launch_pack(E.theta + (int64_t)f * n, n, ts, n, 1, NB, npad, st));
+        TRY(predict_impl(ctx, *E.pr, E.beta + (int64_t)f * P, 1, xbtmp));
+        LK(launch_resid_slot(xbtmp, E.z + (int64_t)f * n, E.y, n, F.r, b, NB, st));
+      } else {
+        LK(launch_pack(zero, P, bs, P, 1, NB, P, st));
+        LK(launch_pack(E.y, n, zs, n, 1, NB, npad, st));
+        LK(launch_pack(zero, n, ts, n, 1, NB, npad, st));
+        LK(launch_pack(zero, n, rs, n, 1, NB, npad, st));
+      }
+      htau[b] = w.tau;
+      hlam[b] = w.lam;
+      hlamn[b] = w.lamnorm;
+      hk0[b] = host_base;
+      hdone[b] = -1;
+      hmask[b] = 1;
+      any = true;
+    }
+    if (!any) return FSQR_OK;
+    CK(cudaMemcpyAsync(d_tau, htau.data(), sizeof(double) * NB, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_lam, hlam.data(), sizeof(double) * NB, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_lamnorm, hlamn.data(), sizeof(double) * NB, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_k0, hk0.data(), sizeof(int) * NB, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_mask, hmask.data(), sizeof(int) * NB, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(F.done, hdone, sizeof(int) * NB, cudaMemcpyHostToDevice, st));
+    LK(launch_slot_init(NB, F, par, d_mask, st));
+    CK(cudaStreamSynchronize(st));  // the host arrays are reused by the next fill
+    for (int b = 0; b < NB; ++b) hmask[b] = 0;
+    return FSQR_OK;
+  };
+  TRY(fill());
+
+  // ---- the iteration as a captured graph of M steps
+  const int K = F.K;
+  const int M = K * std::max(1, (20 + K - 1) / K);
+  const bool prof = ctx->prof;
+  if (prof && !ctx->ev[0])
+    for (int e = 0; e < 6; ++e) CK(cudaEventCreate(&ctx->ev[e]));
+  int per_graph = 1;
+  for (int off = 0; off < M; ++off) per_graph += 4 + (off % K == 0 ? 1 : 0) + (F.qcorr ? 1 : 0);
+  auto enqueue = [&](bool sample) -> cudaError_t {
+    cudaError_t ce = cudaSuccess;
+    for (int off = 0; off < M && ce == cudaSuccess; ++off) {
+      const bool sm = sample && off == M - 1;
+      ce = launch_wquant(NB, F, off, dg, st);
+      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[0], st);
+      if (ce == cudaSuccess) ce = launch_wcol(NB, X, F, off, xt, dg, tsc.rounds, d_err, st);
+      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[1], st);
+      if (off % K == 0 && ce == cudaSuccess) ce = launch_wcheck(NB, F, off, st);
+      if (F.qcorr && ce == cudaSuccess) ce = launch_miss_xb(NB, X, F, off, nullptr, st);
+      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[2], st);
+      if (ce == cudaSuccess) ce = launch_wxbeta(NB, X, F, off, 1, nullptr, scol, wtile, d_err, ctx->num_sms, st);
+      if (sm && ce == cudaSuccess) ce = cudaEventRecord(ctx->ev[3], st);
+    }
+    if (ce == cudaSuccess) ce = launch_advance(it_base, M, st);
+    return ce;
+  };
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = enqueue(false);
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (ce != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return fail(ctx, FSQR_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+  }
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return fail(ctx, FSQR_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+
+  std::vector<int> iters_of(nf, 0), status_of(nf, FSQR_OK);
+  std::vector<double> rep_of((size_t)nf * kReport, 0.0);
+  int64_t max_iter_sum = 0;
+  for (int q = 0; q < nf; ++q) max_iter_sum += E.o->max_iter;
+  const int64_t max_launch = max_iter_sum / M + 3 * (int64_t)nf + 8;
+  int rc = FSQR_OK;
+  int live = 0;
+  for (int b = 0; b < NB; ++b) live += slot_fit[b] >= 0;
+  for (int64_t l = 0; live > 0; ++l) {
+    const bool sample = prof && (l % 4 == 0);
+    ce = sample ? enqueue(true) : cudaGraphLaunch(exec, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hdone, F.done, sizeof(int) * NB, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(hrep, F.report, sizeof(double) * NB * kReport, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+      rc = fail(ctx, FSQR_ECUDA, "wide iteration graph: %s", cudaGetErrorString(ce));
+      break;
+    }
+    host_base += M;
+    ctx->pf.kernel_launches += per_graph;
+    if (sample) {
+      float a = 0.f, b2 = 0.f;
+      if (cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]) == cudaSuccess &&
+          cudaEventElapsedTime(&b2, ctx->ev[2], ctx->ev[3]) == cudaSuccess) {
+        ctx->pf.col_ms += a;
+        ctx->pf.col_samples += 1;
+        ctx->pf.xb_ms += b2;
+        ctx->pf.xb_samples += 1;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    if (E.deadline_ms > 0 && now_ms() > E.deadline_ms) timed_out = true;
+    // move finished fits out of their slots
+    bool freed = false;
+    for (int b = 0; b < NB; ++b) {
+      const int q = slot_fit[b];
+      if (q < 0) continue;
+      const bool fin = hdone[b] >= 0 && hdone[b] != kIdle;
+      if (!fin && !timed_out) continue;
+      const int kf = fin ? hdone[b] : host_base;
+      const int f = fits[q].fit;
+      LK(launch_unpack(F.beta[kf & 1] + b, E.beta + (int64_t)f * P, P, P, 1, NB, st));
+      LK(launch_unpack(F.z + b, E.z + (int64_t)f * n, n, n, 1, NB, st));
+      LK(launch_unpack(F.theta + b, E.theta + (int64_t)f * n, n, n, 1, NB, st));
+      LK(launch_unpack(F.r + b, rfit + (int64_t)q * n, n, n, 1, NB, st));
+      for (int t = 0; t < kReport; ++t) rep_of[(size_t)q * kReport + t] = hrep[b * kReport + t];
+      iters_of[q] = fin ? (int)hrep[b * kReport + 7] : host_base - hk0[b];
+      status_of[q] = fin ? (int)hrep[b * kReport + 5] : FSQR_ETIMEOUT;
+      state[q] = 2;
+      ++finished;
+      slot_fit[b] = -1;
+      hdone[b] = kIdle;
+      freed = true;
+    }
+    if (timed_out) break;
+    if (freed) {
+      CK(cudaMemcpyAsync(F.done, hdone, sizeof(int) * NB, cudaMemcpyHostToDevice, st));
+      TRY(fill());
+    }
+    live = 0;
+    for (int b = 0; b < NB; ++b) live += slot_fit[b] >= 0;
+    if (l > max_launch) {
+      rc = fail(ctx, FSQR_ECUDA, "wide iteration did not stop after %d steps", host_base);
+      break;
+    }
+  }
+  cudaGraphExecDestroy(exec);
+  if (rc != FSQR_OK) return rc;
+  {
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr != 0)
+      return fail(ctx, FSQR_ECUDA, "wide tensor-core pass: a pipeline wait ran out of time (code %d)", herr);
+  }
+  if (!timed_out && finished < nf)
+    return fail(ctx, FSQR_EINVAL, "%d fits could not start (a start refers to a fit outside the solve)",
+                nf - finished);
+  ctx->pf.iterations += host_base;
+  ctx->pf.col_bytes = n * X.p + 8 * n * X.c + 2 * 8 * P * NB;
+  ctx->pf.wide_groups += 1;
+  const double t_solve = now_ms() - t0;
+
+  // ---- per-fit reports: primal value, active count, duality gap (groups of 8)
+  if (E.infos) {
+    double *bfin, *zfin, *rfin, *thfin, *tcd, *tcs, *schk, *summ, *dtaus, *dlams;
+    TRY(wsget(ctx, "r_bfin", (size_t)P * kMaxNB, &bfin));
+    TRY(wsget(ctx, "r_zfin", (size_t)npad * kMaxNB, &zfin));
+    TRY(wsget(ctx, "r_rfin", (size_t)npad * kMaxNB, &rfin));
+    TRY(wsget(ctx, "r_thfin", (size_t)npad * kMaxNB, &thfin));
+    TRY(wsget(ctx, "r_tc", (size_t)npad * kMaxNB, &tcd));
+    TRY(wsget(ctx, "r_tcs", kMaxNB, &tcs));
+    TRY(wsget(ctx, "r_schk", (size_t)P * kMaxNB, &schk));
+    TRY(wsget(ctx, "r_summ", (size_t)kMaxNB * 8, &summ));
+    TRY(wsget(ctx, "r_taus", kMaxNB, &dtaus));
+    TRY(wsget(ctx, "r_lams", kMaxNB, &dlams));
+    Fits Fx = pass_fits(ctx, X);
+    for (int q0 = 0; q0 < nf; q0 += kMaxNB) {
+      const int nb = std::min(kMaxNB, nf - q0);
+      const int NB8 = nb_template(nb);
+      double ht[kMaxNB], hl[kMaxNB];
+      for (int u = 0; u < kMaxNB; ++u) {
+        ht[u] = u < nb ? fits[q0 + u].tau : 0.5;
+        hl[u] = u < nb ? fits[q0 + u].lam : 0.0;
+      }
+      CK(cudaMemsetAsync(bfin, 0, sizeof(double) * P * NB8, st));
+      CK(cudaMemsetAsync(zfin, 0, sizeof(double) * npad * NB8, st));
+      CK(cudaMemsetAsync(rfin, 0, sizeof(double) * npad * NB8, st));
+      CK(cudaMemsetAsync(thfin, 0, sizeof(double) * npad * NB8, st));
+      for (int u = 0; u < nb; ++u) {
+        const int f = fits[q0 + u].fit;
+        LK(launch_pack(E.beta + (int64_t)f * P, P, bfin + u, P, 1, NB8, P, st));
+        LK(launch_pack(E.z + (int64_t)f * n, n, zfin + u, n, 1, NB8, npad, st));
+        LK(launch_pack(E.theta + (int64_t)f * n, n, thfin + u, n, 1, NB8, npad, st));
+        LK(launch_pack(rfit + (int64_t)(q0 + u) * n, n, rfin + u, n, 1, NB8, npad, st));
+      }
+      CK(cudaMemcpyAsync(dtaus, ht, sizeof ht, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(dlams, hl, sizeof hl, cudaMemcpyHostToDevice, st));
+      const double *schk_use = nullptr, *tc_use = nullptr;
+      if (E.gap_defined) {
+        LK(launch_dual_point(NB8, thfin, n, npad, dtaus, nb, tcd, tcs, st));
+        LK(launch_col_pass(A_XT, NB8, X, Fx, 0, tcd, tcs, schk, nullptr, st));
+        schk_use = schk;
+        tc_use = tcd;
+      }
+      LK(launch_summary(NB8, nb, n, P, E.y, zfin, rfin, bfin, E.omega, dtaus, dlams, schk_use, tc_use, E.o->ridge,
+                        summ, st));
+      double hs[kMaxNB * 8];
+      CK(cudaMemcpyAsync(hs, summ, sizeof(double) * kMaxNB * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int u = 0; u < nb; ++u) {
+        const int q = q0 + u;
+        fsqr_info &I = E.infos[fits[q].fit];
+        const double *rp = &rep_of[(size_t)q * kReport];
+        I.status = status_of[q];
+        I.iters = iters_of[q];
+        I.kkt = rp[0];
+        I.r_p = rp[1];
+        I.r_z = rp[2];
+        I.r_beta = rp[3];
+        I.r_1 = rp[4];
+        I.primal = hs[u * 8 + 0] + hs[u * 8 + 1];
+        I.active = (int64_t)hs[u * 8 + 2];
+        if (E.gap_defined) {
+          I.dual = hs[u * 8 + 3] * hs[u * 8 + 4];
+          I.gap = (I.primal - I.dual) / (1.0 + fabs(I.primal) + fabs(I.dual));
+        } else {
+          I.dual = NAN;
+          I.gap = NAN;
+        }
+        I.lambda = fits[q].lam;
+        I.lambda_max = fits[q].lamnorm;
+        I.mu = E.mu;
+        I.t_solve_ms = t_solve;
+      }
+    }
+  } else {
+    CK(cudaStreamSynchronize(st));
+  }
+  return timed_out ? FSQR_ETIMEOUT : FSQR_OK;
+}
+
 // Autotuner of the fits advanced together per X pass (opts.max_group = 0).
 // For each candidate g (1, 2, 3, 4 and min(B, 8), up to B), the first g
 // fits run cold for I1 and then I2 iterations; the difference of the two
@@ -801,9 +1276,17 @@ int tune_group(fsqr_ctx *ctx, const SolveEnv &E, int B, int n_lambda, const doub
                const double *lambdas, const std::vector<double> &lmax, int *out) {
   const Dsg &X = E.pr->X;
   const fsqr_opts *o = E.o;
-  char key[160];
-  snprintf(key, sizeof key, "%lld/%lld/%lld/%d/%d/%d/%d/%d", (long long)X.n, (long long)X.p, (long long)X.c,
-           X.fmt, o->precision, o->digits, B, o->warm);
+  // the partition enters the key: eta_g and the per-block work depend on it
+  uint64_t bph = 1469598103934665603ull;
+  {
+    std::vector<int64_t> hbp(E.G + 1);
+    if (cudaMemcpy(hbp.data(), E.d_bp, sizeof(int64_t) * (E.G + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(ctx, FSQR_ECUDA, "block partition read-back failed");
+    for (int64_t v : hbp) bph = (bph ^ (uint64_t)v) * 1099511628211ull;
+  }
+  char key[200];
+  snprintf(key, sizeof key, "%lld/%lld/%lld/%d/%d/%d/%d/%d/%d/%llx", (long long)X.n, (long long)X.p,
+           (long long)X.c, X.fmt, o->precision, o->digits, B, o->warm, E.G, (unsigned long long)bph);
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) {
     *out = it->second;
@@ -813,7 +1296,11 @@ int tune_group(fsqr_ctx *ctx, const SolveEnv &E, int B, int n_lambda, const doub
   std::vector<int> cand;
   for (int g : {1, 2, 3, 4, std::min(B, kMaxNB)})
     if (g <= B && (cand.empty() || g > cand.back())) cand.push_back(g);
-  const int gmax = cand.back();
+  if (tc_eligible(X, o->precision)) {  // wide slots (their fits run min(B, g) at a time)
+    if (B > kMaxNB) cand.push_back(16);
+    if (B > 16) cand.push_back(kWideMax);
+  }
+  const int gmax = std::min(B, cand.back());
   if (cand.size() == 1) {
     *out = gmax;
     ctx->pf.tuned_group = gmax;
@@ -843,9 +1330,22 @@ int tune_group(fsqr_ctx *ctx, const SolveEnv &E, int B, int n_lambda, const doub
   int bestg = cand[0];
   const fsqr_profile keep = ctx->pf;
   for (int g : cand) {
+    const int gf = std::min(g, B);
+    std::vector<WideFit> wf;
+    for (int q = 0; q < gf && g > kMaxNB; ++q) {
+      const int t = q / n_lambda;
+      WideFit w{};
+      w.tau = taus[t];
+      w.lam = lambdas[q];
+      w.lamnorm = lmax[t] > 0.0 ? lmax[t] : 1.0;
+      w.fit = q;
+      w.from = -1;
+      w.given = false;
+      wf.push_back(w);
+    }
     GroupSpec gs{};
-    gs.nb = g;
-    for (int q = 0; q < g; ++q) {
+    gs.nb = std::min(g, kMaxNB);
+    for (int q = 0; q < gs.nb; ++q) {
       const int t = q / n_lambda;
       gs.tau[q] = taus[t];
       gs.lam[q] = lambdas[q];
@@ -858,7 +1358,8 @@ int tune_group(fsqr_ctx *ctx, const SolveEnv &E, int B, int n_lambda, const doub
       tmp.max_iter = r == 0 ? I1 : I2;
       CK(cudaStreamSynchronize(st));
       const double t0 = now_ms();
-      TRY(solve_group(ctx, E2, gs));
+      if (g > kMaxNB) TRY(solve_wide(ctx, E2, g, wf));
+      else TRY(solve_group(ctx, E2, gs));
       CK(cudaStreamSynchronize(st));
       w[r] = now_ms() - t0;
     }
@@ -880,10 +1381,14 @@ int tune_group(fsqr_ctx *ctx, const SolveEnv &E, int B, int n_lambda, const doub
   return FSQR_OK;
 }
 
+// lamnorm_in (host, n_tau; may be NULL): the lambda_max(tau) that divides R_b,
+// in place of the one of omega (the reweighted fits of LLA keep the first
+// fit's). eta_out (may be NULL): receives the eta_g used.
 int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_tau,
                    const double *taus, int n_lambda, const double *lambdas, const double *omega,
                    const int64_t *block_ptr, int G, const fsqr_opts *opts, double *beta, double *z,
-                   double *theta, fsqr_info *infos) {
+                   double *theta, fsqr_info *infos, const double *lamnorm_in = nullptr,
+                   std::vector<double> *eta_out = nullptr) {
   const double t0 = now_ms();
   TRY(check_opts(ctx, opts, G));
   if (n_tau < 1 || n_lambda < 1) return fail(ctx, FSQR_EINVAL, "n_tau and n_lambda must be >= 1");
@@ -923,8 +1428,12 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
     TRY(eta_impl(ctx, pr, block_ptr, G, mu, opts->eta_margin, opts->power_iters, opts->power_tol,
                  eta.data()));
   }
+  if (eta_out) *eta_out = eta;
   std::vector<double> lmax(n_tau);
-  for (int t = 0; t < n_tau; ++t) TRY(lambda_max_impl(ctx, pr, y, taus[t], omega, &lmax[t]));
+  for (int t = 0; t < n_tau; ++t) {
+    if (lamnorm_in) lmax[t] = lamnorm_in[t];
+    else TRY(lambda_max_impl(ctx, pr, y, taus[t], omega, &lmax[t]));
+  }
   if (opts->warm == FSQR_WARM_LEARNED)
     for (int t = 0; t < n_tau; ++t)
       for (int l = 0; l < n_lambda; ++l) {
@@ -941,7 +1450,7 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
   E.G = G;
   E.mu = mu;
   E.ymax = ymax;
-  E.gap_defined = (P == 1) || (om[1] > 0.0);
+  E.gap_defined = ((P == 1) || (om[1] > 0.0)) && opts->ridge == 0.0;
   E.o = opts;
   E.beta = beta;
   E.z = z;
@@ -962,6 +1471,32 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
   const int B = n_tau * n_lambda;
   int mg = opts->max_group;
   if (mg == 0) TRY(tune_group(ctx, E, B, n_lambda, taus, lambdas, lmax, &mg));
+  if (mg > kMaxNB && tc_eligible(X, opts->precision)) {
+    // wide slots: every fit streams through 16 or 32 slots of one solve
+    std::vector<WideFit> wf;
+    for (int t = 0; t < n_tau; ++t)
+      for (int l = 0; l < n_lambda; ++l) {
+        const int f = t * n_lambda + l;
+        WideFit w{};
+        w.tau = taus[t];
+        w.lam = lambdas[f];
+        w.lamnorm = lmax[t] > 0.0 ? lmax[t] : 1.0;
+        w.fit = f;
+        w.from = (opts->warm == FSQR_WARM_PATH && l > 0) ? f - 1 : -1;
+        w.given = opts->warm == FSQR_WARM_GIVEN || opts->warm == FSQR_WARM_LEARNED;
+        wf.push_back(w);
+      }
+    const int rcw = solve_wide(ctx, E, mg <= 16 ? 16 : kWideMax, wf);
+    if (rcw != FSQR_OK && rcw != FSQR_ETIMEOUT) return rcw;
+    int worstw = FSQR_OK;
+    if (infos)
+      for (int f = 0; f < B; ++f) {
+        infos[f].t_setup_ms = t_setup;
+        if (worstw == FSQR_OK && infos[f].status != FSQR_OK) worstw = infos[f].status;
+      }
+    return infos ? worstw : rcw;
+  }
+  mg = std::min(mg, kMaxNB);
   std::vector<GroupSpec> groups;
   if (opts->warm == FSQR_WARM_PATH) {
     for (int l = 0; l < n_lambda; ++l)
@@ -1007,6 +1542,214 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
   return worst;
 }
 
+// s_out (host, nb x P) = X~^T theta_b for nb <= 8 fits whose theta sit at
+// th + b*n (device, fit-major): one full column pass.
+int full_xt(fsqr_ctx *ctx, const Prep &pr, const double *th, int nb, std::vector<double> &s_out) {
+  const Dsg &X = pr.X;
+  const int64_t n = X.n, npad = pad16(n), P = X.P;
+  cudaStream_t st = ctx->stream;
+  const int NB = nb_template(nb);
+  double *il, *sums, *s;
+  TRY(wsget(ctx, "sc_thil", (size_t)npad * kMaxNB, &il));
+  TRY(wsget(ctx, "sc_sums", kMaxNB, &sums));
+  TRY(wsget(ctx, "sc_s", (size_t)P * kMaxNB, &s));
+  CK(cudaMemsetAsync(il, 0, sizeof(double) * npad * NB, st));
+  CK(cudaMemsetAsync(sums, 0, sizeof(double) * kMaxNB, st));
+  LK(launch_pack(th, n, il, n, nb, NB, npad, st));
+  LK(launch_sum_cols(th, n, n, nb, sums, nullptr, st));
+  Fits Fx = pass_fits(ctx, X);
+  LK(launch_col_pass(A_XT, NB, X, Fx, 0, il, sums, s, nullptr, st));
+  std::vector<double> h((size_t)P * NB);
+  CK(cudaMemcpyAsync(h.data(), s, sizeof(double) * P * NB, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  s_out.assign((size_t)nb * P, 0.0);
+  for (int b = 0; b < nb; ++b)
+    for (int64_t j = 0; j < P; ++j) s_out[(size_t)b * P + j] = h[(size_t)j * NB + b];
+  return FSQR_OK;
+}
+
+// Sequential strong rule along each tau's lambda path (opts.screen with
+// FSQR_WARM_PATH). At stage l, stored column j is left out of the fits of
+// every tau when |s_j| < omega_j (2 lambda_l - lambda_{l-1}) for each tau,
+// with s = X~^T theta of the tau's fit at lambda_{l-1} (at l = 0 the
+// lambda_max direction, lambda_{-1} = lambda_max), and beta_j = 0 there. The
+// stage's fits are solved on the kept columns only (same standardisation,
+// blocks, eta and lambda_max), each from its predecessor's solution; then
+// s = X~^T theta over ALL columns is checked: a left-out column with
+// (|s_j| - lambda_j)_+ / lambda_max > tol is put back and the stage re-solved.
+// So every returned fit meets the stop test on the full design.
+int fit_path_screened(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_tau, const double *taus,
+                      int n_lambda, const double *lambdas, const double *omega, const int64_t *block_ptr, int G,
+                      const fsqr_opts *opts, double *beta, double *z, double *theta, fsqr_info *infos) {
+  const double t0 = now_ms();
+  TRY(check_opts(ctx, opts, G));
+  if (n_tau < 1 || n_lambda < 1 || !taus || !lambdas) return fail(ctx, FSQR_EINVAL, "bad tau/lambda grid");
+  if (!y || !omega || !beta || !z || !theta) return fail(ctx, FSQR_EINVAL, "NULL array argument");
+  if (n_tau > kMaxNB) return fail(ctx, FSQR_EINVAL, "screening takes at most %d quantiles", kMaxNB);
+  Prep pr;
+  TRY(prepare(ctx, Xd, &pr, opts->precision != FSQR_FP64));
+  const Dsg &X = pr.X;
+  const int64_t n = X.n, P = X.P, c = X.c, p = X.p, npad = pad16(n);
+  TRY(check_blocks(ctx, block_ptr, G, P));
+  cudaStream_t st = ctx->stream;
+  double ymax, ysd;
+  TRY(y_stats(ctx, y, n, &ymax, &ysd));
+  const double mu = opts->mu > 0.0 ? opts->mu : 1.0 / ((double)n * (ysd > 0.0 ? ysd : 1.0));
+  std::vector<double> eta(G);
+  if (opts->eta) for (int g = 0; g < G; ++g) eta[g] = opts->eta[g];
+  else TRY(eta_impl(ctx, pr, block_ptr, G, mu, opts->eta_margin, opts->power_iters, opts->power_tol, eta.data()));
+  // lambda_max and its direction s_dir = X~^T v / n per tau
+  std::vector<double> lmax(n_tau), sprev((size_t)n_tau * P), hom(P);
+  for (int t = 0; t < n_tau; ++t) {
+    LmaxDev L;
+    TRY(lambda_max_dev(ctx, pr, y, taus[t], omega, &L));
+    double lm;
+    CK(cudaMemcpyAsync(&lm, L.o, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(sprev.data() + (size_t)t * P, L.s, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    lmax[t] = lm > 0.0 ? lm : 1.0;
+    for (int64_t j = 0; j < P; ++j) sprev[(size_t)t * P + j] /= (double)n;
+  }
+  CK(cudaMemcpyAsync(hom.data(), omega, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  // work buffers
+  int32_t *d_sel, *d_idx;
+  uint8_t *g_red;
+  double *m_red, *s_red, *om_red, *b_red, *z_st, *t_st;
+  TRY(wsget(ctx, "sc_sel", (size_t)std::max<int64_t>(p, 1), &d_sel));
+  TRY(wsget(ctx, "sc_idx", (size_t)P, &d_idx));
+  TRY(wsget(ctx, "sc_geno", (size_t)std::max<int64_t>(p * Xd->geno_ld, 16), &g_red));
+  TRY(wsget(ctx, "sc_mean", (size_t)(c + p), &m_red));
+  TRY(wsget(ctx, "sc_sd", (size_t)(c + p), &s_red));
+  TRY(wsget(ctx, "sc_om", (size_t)P, &om_red));
+  TRY(wsget(ctx, "sc_beta", (size_t)n_tau * P, &b_red));
+  TRY(wsget(ctx, "sc_z", (size_t)n_tau * n, &z_st));
+  TRY(wsget(ctx, "sc_th", (size_t)n_tau * n, &t_st));
+  std::vector<double> hbeta((size_t)P);
+  std::vector<fsqr_info> st_info(n_tau);
+  int worst = FSQR_OK;
+  for (int l = 0; l < n_lambda; ++l) {
+    std::vector<char> keep((size_t)p, 0);
+    for (int t = 0; t < n_tau; ++t) {
+      const int f = t * n_lambda + l;
+      const double lam = lambdas[f], lprev = l ? lambdas[f - 1] : lmax[t];
+      if (l) CK(cudaMemcpy(hbeta.data(), beta + (int64_t)(f - 1) * P, sizeof(double) * P, cudaMemcpyDeviceToHost));
+      for (int64_t s = 0; s < p; ++s) {
+        const int64_t j = 1 + c + s;
+        if (hom[j] == 0.0 || fabs(sprev[(size_t)t * P + j]) >= hom[j] * (2.0 * lam - lprev) ||
+            (l && hbeta[j] != 0.0))
+          keep[s] = 1;
+      }
+    }
+    for (int round = 0;; ++round) {
+      std::vector<int32_t> sel, idx;
+      for (int64_t j = 0; j <= c; ++j) idx.push_back((int32_t)j);
+      for (int64_t s = 0; s < p; ++s)
+        if (keep[s]) { sel.push_back((int32_t)s); idx.push_back((int32_t)(1 + c + s)); }
+      const int64_t ns = (int64_t)sel.size(), Pr = 1 + c + ns;
+      ctx->pf.screen_kept += ns * n_tau;
+      ctx->pf.screen_total += p * n_tau;
+      // reduced design: kept stored columns, the full design's statistics
+      CK(cudaMemcpyAsync(d_idx, idx.data(), sizeof(int32_t) * Pr, cudaMemcpyHostToDevice, st));
+      if (ns) CK(cudaMemcpyAsync(d_sel, sel.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st));
+      LK(launch_gather_cols(static_cast<const uint8_t *>(Xd->geno), Xd->geno_ld, d_sel, ns, g_red, st));
+      if (c) {
+        CK(cudaMemcpyAsync(m_red, pr.mean, sizeof(double) * c, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(s_red, pr.sd, sizeof(double) * c, cudaMemcpyDeviceToDevice, st));
+      }
+      LK(launch_index_copy(pr.mean + c, 0, d_sel, ns, 1, m_red + c, 0, 0, st));
+      LK(launch_index_copy(pr.sd + c, 0, d_sel, ns, 1, s_red + c, 0, 0, st));
+      LK(launch_index_copy(omega, 0, d_idx, Pr, 1, om_red, 0, 0, st));
+      std::vector<int64_t> bpr(1, 0);
+      std::vector<double> etar;
+      {
+        size_t q = 0;
+        for (int g = 0; g < G; ++g) {
+          int64_t cnt = 0;
+          while (q < idx.size() && idx[q] < block_ptr[g + 1]) { ++cnt; ++q; }
+          if (cnt) { bpr.push_back(bpr.back() + cnt); etar.push_back(eta[g]); }
+        }
+      }
+      const int Gr = (int)etar.size();
+      // starts: the predecessor's solution (round 0) or the stage's own last iterate
+      for (int t = 0; t < n_tau; ++t) {
+        const int f = t * n_lambda + l;
+        const int src = (round == 0) ? (l ? f - 1 : -1) : f;
+        if (src < 0) {
+          CK(cudaMemsetAsync(b_red + (int64_t)t * Pr, 0, sizeof(double) * Pr, st));
+          CK(cudaMemcpyAsync(z_st + (int64_t)t * n, y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+          CK(cudaMemsetAsync(t_st + (int64_t)t * n, 0, sizeof(double) * n, st));
+        } else {
+          LK(launch_index_copy(beta + (int64_t)src * P, 0, d_idx, Pr, 1, b_red + (int64_t)t * Pr, 0, 0, st));
+          CK(cudaMemcpyAsync(z_st + (int64_t)t * n, z + (int64_t)src * n, sizeof(double) * n,
+                             cudaMemcpyDeviceToDevice, st));
+          CK(cudaMemcpyAsync(t_st + (int64_t)t * n, theta + (int64_t)src * n, sizeof(double) * n,
+                             cudaMemcpyDeviceToDevice, st));
+        }
+      }
+      fsqr_design Xr = *Xd;
+      Xr.p = ns;
+      Xr.geno = ns ? g_red : nullptr;
+      Xr.col_mean = m_red;
+      Xr.col_sd = s_red;
+      fsqr_opts o2 = *opts;
+      o2.warm = FSQR_WARM_GIVEN;
+      o2.screen = 0;
+      o2.eta = etar.data();
+      o2.mu = mu;
+      std::vector<double> lam_st(n_tau);
+      for (int t = 0; t < n_tau; ++t) lam_st[t] = lambdas[t * n_lambda + l];
+      memset(st_info.data(), 0, sizeof(fsqr_info) * n_tau);
+      const int rc = fit_batch_impl(ctx, &Xr, y, n_tau, taus, 1, lam_st.data(), om_red, bpr.data(), Gr, &o2, b_red,
+                                    z_st, t_st, st_info.data(), lmax.data(), nullptr);
+      if (rc != FSQR_OK && rc != FSQR_ENOCONV && rc != FSQR_ETIMEOUT && rc != FSQR_ENUMERIC) return rc;
+      // back to the full index space
+      for (int t = 0; t < n_tau; ++t) {
+        const int f = t * n_lambda + l;
+        CK(cudaMemsetAsync(beta + (int64_t)f * P, 0, sizeof(double) * P, st));
+        LK(launch_index_copy(b_red + (int64_t)t * Pr, 0, d_idx, Pr, 1, beta + (int64_t)f * P, 0, 1, st));
+        CK(cudaMemcpyAsync(z + (int64_t)f * n, z_st + (int64_t)t * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(theta + (int64_t)f * n, t_st + (int64_t)t * n, sizeof(double) * n,
+                           cudaMemcpyDeviceToDevice, st));
+      }
+      // the stop test's R_b over the left-out columns, on the full design
+      std::vector<double> sfull;
+      TRY(full_xt(ctx, pr, t_st, n_tau, sfull));
+      bool viol = false;
+      for (int t = 0; t < n_tau; ++t) {
+        const int f = t * n_lambda + l;
+        double dmax = 0.0;
+        for (int64_t s = 0; s < p; ++s) {
+          if (keep[s]) continue;
+          const int64_t j = 1 + c + s;
+          const double d = fmax(fabs(sfull[(size_t)t * P + j]) - lambdas[f] * hom[j], 0.0) / lmax[t];
+          if (d > opts->tol) { keep[s] = 1; viol = true; }
+          dmax = fmax(dmax, d);
+        }
+        st_info[t].r_beta = fmax(st_info[t].r_beta, dmax);
+        st_info[t].kkt = fmax(st_info[t].kkt, dmax);
+        for (int64_t j = 0; j < P; ++j) sprev[(size_t)t * P + j] = sfull[(size_t)t * P + j];
+      }
+      if (!viol || round >= 8) {
+        for (int t = 0; t < n_tau; ++t) {
+          const int f = t * n_lambda + l;
+          if (infos) {
+            infos[f] = st_info[t];
+            infos[f].t_setup_ms = 0.0;
+            if (viol && infos[f].status == FSQR_OK) infos[f].status = FSQR_ENOCONV;
+          }
+          const int s_f = infos ? infos[f].status : FSQR_OK;
+          if (worst == FSQR_OK && s_f != FSQR_OK) worst = s_f;
+        }
+        break;
+      }
+    }
+  }
+  if (infos)
+    for (int f = 0; f < n_tau * n_lambda; ++f) infos[f].t_solve_ms = now_ms() - t0;
+  return worst;
+}
+
 // out[b*n + i] = x~_i^T beta_b for B coefficient vectors (FP64 path).
 int predict_impl(fsqr_ctx *ctx, const Prep &pr, const double *beta, int B, double *out) {
   const Dsg &X = pr.X;
@@ -1025,6 +1768,10 @@ int predict_impl(fsqr_ctx *ctx, const Prep &pr, const double *beta, int B, doubl
   TRY(wsget(ctx, "p_done", kMaxNB, &done));
   F.done = done;
   CK(cudaMemsetAsync(done, 0xff, sizeof(int) * kMaxNB, st));
+  if (X.mptr) {
+    TRY(wsget(ctx, "p_qcorr", (size_t)npad * kMaxNB, &F.qcorr));
+    CK(cudaMemsetAsync(F.qcorr, 0, sizeof(double) * npad * kMaxNB, st));
+  }
   double *bg;
   TRY(wsget(ctx, "p_bg", (size_t)P * kMaxNB, &bg));
   CK(cudaMemsetAsync(bg, 0, sizeof(double) * P * kMaxNB, st));
@@ -1035,6 +1782,7 @@ int predict_impl(fsqr_ctx *ctx, const Prep &pr, const double *beta, int B, doubl
     LK(launch_pack(beta + (int64_t)b0 * P, P, bg, P, nb, NB, P, st));
     LK(launch_col_pass(A_LIST, NB, X, F, 0, nullptr, nullptr, nullptr, bg, st));
     LK(launch_xbeta(NB, X, F, 0, bg, st));
+    if (F.qcorr) LK(launch_miss_xb(NB, X, F, 0, bg, st));
     LK(launch_gather_xb(NB, F, out + (int64_t)b0 * n, n, nb, st));
   }
   CK(cudaStreamSynchronize(st));
@@ -1065,6 +1813,7 @@ void fsqr_opts_default(fsqr_opts *o) {
   o->digits = 4;
   o->max_group = 4;
   o->timeout_ms = 0;
+  o->ridge = 0.0;
 }
 
 int fsqr_create(fsqr_ctx **out, int device, void *cuda_stream) {
@@ -1167,6 +1916,11 @@ int fsqr_fit_batch(fsqr_ctx *ctx, const fsqr_design *X, const double *y, int n_t
     infos = local.data();
   }
   memset(infos, 0, sizeof(fsqr_info) * (size_t)std::max(0, n_tau * n_lambda));
+  if (opts && opts->screen) {
+    if (opts->warm != FSQR_WARM_PATH) return fail(ctx, FSQR_EINVAL, "opts.screen needs FSQR_WARM_PATH");
+    return fit_path_screened(ctx, X, y, n_tau, taus, n_lambda, lambdas, omega, block_ptr, G, opts, beta, z,
+                             theta, infos);
+  }
   return fit_batch_impl(ctx, X, y, n_tau, taus, n_lambda, lambdas, omega, block_ptr, G, opts,
                         beta, z, theta, infos);
 }
@@ -1180,6 +1934,54 @@ int fsqr_fit(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau, d
   fsqr_info tmp;
   return fsqr_fit_batch(ctx, X, y, 1, &tau, 1, &lambda, omega, block_ptr, G, opts, beta, z, theta,
                         info ? info : &tmp);
+}
+
+int fsqr_fit_lla(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau, double lambda,
+                 const double *omega, const int64_t *block_ptr, int G, int penalty, double a, int L,
+                 const fsqr_opts *opts, double *beta, double *z, double *theta, double *lam_out,
+                 fsqr_info *info) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (penalty != FSQR_PEN_SCAD && penalty != FSQR_PEN_MCP)
+    return fail(ctx, FSQR_EINVAL, "penalty must be FSQR_PEN_SCAD or FSQR_PEN_MCP");
+  if (!(a > (penalty == FSQR_PEN_SCAD ? 2.0 : 1.0)) || isinf(a))
+    return fail(ctx, FSQR_EINVAL, "a must be finite and > %d for this penalty", penalty == FSQR_PEN_SCAD ? 2 : 1);
+  if (L < 0) return fail(ctx, FSQR_EINVAL, "L must be >= 0");
+  if (!(lambda > 0.0) || isinf(lambda)) return fail(ctx, FSQR_EINVAL, "lambda must be finite and > 0");
+  if (!opts) return fail(ctx, FSQR_EINVAL, "opts is NULL");
+  fsqr_info step{};
+  std::vector<double> eta;
+  // step 0: the weighted-l1 fit at lambda omega
+  int rc = fit_batch_impl(ctx, X, y, 1, &tau, 1, &lambda, omega, block_ptr, G, opts, beta, z, theta, &step,
+                          nullptr, &eta);
+  if (rc != FSQR_OK && rc != FSQR_ENOCONV && rc != FSQR_ETIMEOUT) return rc;
+  int iters = step.iters;
+  const double lamnorm = step.lambda_max;
+  const int64_t P = 1 + X->c + X->p;
+  double *w;
+  TRY(wsget(ctx, "lla_w", (size_t)P, &w));
+  fsqr_opts o = *opts;
+  o.eta = eta.data();
+  o.warm = FSQR_WARM_GIVEN;
+  o.max_group = 1;
+  for (int l = 1; l <= L && (rc == FSQR_OK || rc == FSQR_ENOCONV); ++l) {
+    // lambda omega'_j = omega_j p'_lambda(|beta~_j|), from the previous step's fit
+    LK(launch_lla_weights(beta, omega, P, lambda, a, penalty, 1.0 / lambda, w, ctx->stream));
+    rc = fit_batch_impl(ctx, X, y, 1, &tau, 1, &lambda, w, block_ptr, G, &o, beta, z, theta, &step, &lamnorm,
+                        nullptr);
+    if (rc != FSQR_OK && rc != FSQR_ENOCONV && rc != FSQR_ETIMEOUT) return rc;
+    iters += step.iters;
+  }
+  if (lam_out) {
+    if (L == 0) LK(launch_lla_weights(beta, omega, P, lambda, a, 0, 1.0, lam_out, ctx->stream));
+    else LK(launch_lla_weights(w, nullptr, P, lambda, a, -1, lambda, lam_out, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (info) {
+    *info = step;
+    info->iters = iters;
+  }
+  return rc;
 }
 
 int fsqr_fit_batch_host(fsqr_ctx *ctx, const fsqr_design *X, const double *y, int n_tau,
@@ -1307,7 +2109,7 @@ int fsqr_kkt(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, double tau, 
     schk_use = schk;
     tc_use = tc;
   }
-  LK(launch_summary(1, 1, n, P, y, ypad, xb, beta, omega, dt, dl, schk_use, tc_use, summ, st));
+  LK(launch_summary(1, 1, n, P, y, ypad, xb, beta, omega, dt, dl, schk_use, tc_use, 0.0, summ, st));
   double hs[8];
   CK(cudaMemcpyAsync(hs, summ, sizeof hs, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1340,6 +2142,77 @@ int fsqr_predict(fsqr_ctx *ctx, const fsqr_design *Xd, const double *beta, int B
   Prep pr;
   TRY(prepare(ctx, Xd, &pr, false));
   return predict_impl(ctx, pr, beta, B, out);
+}
+
+int fsqr_path_stats(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int B, const double *taus,
+                    const double *beta, double *loss, int64_t *active, double *hbic) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (B < 1 || !y || !taus || !beta) return fail(ctx, FSQR_EINVAL, "B >= 1, y, taus and beta are required");
+  for (int b = 0; b < B; ++b)
+    if (!(taus[b] > 0.0 && taus[b] < 1.0)) return fail(ctx, FSQR_EINVAL, "tau must be in (0,1)");
+  Prep pr;
+  TRY(prepare(ctx, Xd, &pr, false));
+  const int64_t n = pr.X.n, P = pr.X.P;
+  double *q, *dt, *st;
+  TRY(wsget(ctx, "ps_q", (size_t)B * n, &q));
+  TRY(wsget(ctx, "ps_tau", (size_t)B, &dt));
+  TRY(wsget(ctx, "ps_out", (size_t)2 * B, &st));
+  TRY(predict_impl(ctx, pr, beta, B, q));
+  CK(cudaMemcpyAsync(dt, taus, sizeof(double) * B, cudaMemcpyHostToDevice, ctx->stream));
+  LK(launch_path_stats(q, y, dt, n, beta, P, B, st, ctx->stream));
+  std::vector<double> h((size_t)2 * B);
+  CK(cudaMemcpyAsync(h.data(), st, sizeof(double) * 2 * B, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  // HBIC with C_n = log p over the P - 1 candidate columns
+  const double pen = (n > 1 ? log(log((double)n)) : 0.0) / (double)n * log((double)std::max<int64_t>(P - 1, 1));
+  for (int b = 0; b < B; ++b) {
+    if (loss) loss[b] = h[2 * b] / (double)n;
+    if (active) active[b] = (int64_t)h[2 * b + 1];
+    if (hbic) hbic[b] = log(h[2 * b]) + h[2 * b + 1] * pen;
+  }
+  return FSQR_OK;
+}
+
+int fsqr_interval_coverage(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, const double *beta_lo,
+                           const double *beta_hi, double *coverage, double *width, int64_t *crossings) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (!y || !beta_lo || !beta_hi) return fail(ctx, FSQR_EINVAL, "y, beta_lo and beta_hi are required");
+  Prep pr;
+  TRY(prepare(ctx, Xd, &pr, false));
+  const int64_t n = pr.X.n;
+  double *q, *st;
+  TRY(wsget(ctx, "cv_q", (size_t)2 * n, &q));
+  TRY(wsget(ctx, "cv_out", 3, &st));
+  TRY(predict_impl(ctx, pr, beta_lo, 1, q));
+  TRY(predict_impl(ctx, pr, beta_hi, 1, q + n));
+  LK(launch_coverage(q, q + n, y, n, st, ctx->stream));
+  double h[3];
+  CK(cudaMemcpyAsync(h, st, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (coverage) *coverage = h[0] / (double)n;
+  if (width) *width = h[1] / (double)n;
+  if (crossings) *crossings = (int64_t)h[2];
+  return FSQR_OK;
+}
+
+int fsqr_wait_selftest(fsqr_ctx *ctx, int64_t budget_cycles, int arrive, int *wait_ok) {
+  if (!ctx) return FSQR_EINVAL;
+  TRY(enter(ctx));
+  if (budget_cycles < 0 || budget_cycles > (int64_t)4000000000LL)
+    return fail(ctx, FSQR_EINVAL, "budget_cycles must be in 0..4e9");
+  int *d;
+  TRY(wsget(ctx, "selftest", 2, &d));
+  CK(cudaMemsetAsync(d, 0, 2 * sizeof(int), ctx->stream));
+  LK(launch_wait_selftest((long long)budget_cycles, arrive ? 1 : 0, d, d + 1, ctx->stream));
+  int h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (wait_ok) *wait_ok = h[1];
+  if (h[0] != 0) return fail(ctx, FSQR_ETIMEOUT, "device wait ran out of its %lld-cycle budget (code %d)",
+                             (long long)budget_cycles, h[0]);
+  return FSQR_OK;
 }
 
 int fsqr_profile_enable(fsqr_ctx *ctx, int on) {
@@ -1671,8 +2544,8 @@ int fsqr_lambda_max_noalloc(fsqr_ctx *ctx, const fsqr_design *d, const double *y
   CK(cudaStreamSynchronize(st));
   if (hmiss > 0)
     return fail(ctx, FSQR_EINVAL,
-                "%d missing genotype entries: mean imputation of missing entries is not "
-                "supported by this library",
+                "%d missing genotype entries: this entry point has no room for the per-column "
+                "lists that mean imputation needs; use fsqr_lambda_max",
                 hmiss);
   const int64_t n = X.n, npad = pad16(n);
   int64_t k = (int64_t)ceil((double)n * tau);

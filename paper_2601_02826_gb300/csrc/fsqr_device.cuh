@@ -87,6 +87,24 @@ __device__ void col_finalize(const Fits &F) {
   }
 }
 
+// sum of v[i*NB + b] over the missing samples i of stored column s (0-based);
+// 0 when the design has no missing entries.
+__device__ __forceinline__ double miss_dot(const Dsg &X, int64_t s, const double *v, int NB, int b) {
+  if (X.mptr == nullptr) return 0.0;
+  double acc = 0.0;
+  const int64_t e1 = X.mptr[s + 1];
+  for (int64_t e = X.mptr[s]; e < e1; ++e) acc += v[(int64_t)X.midx[e] * NB + b];
+  return acc;
+}
+
+// Fixed-point integer of v (already scaled): v rounded to the nearest
+// integer. Finite iterates always give |v| < 2^44 here; a NaN or infinite
+// iterate gives 0, so that digit extraction stays in range while the stop
+// test reports the non-finite value.
+__device__ __forceinline__ long long fixed_point(double v) {
+  return (fabs(v) < 4.0e18) ? __double2ll_rn(v) : 0LL;
+}
+
 // dist(t, d rho_tau(z)): {tau} for z > 0, {tau-1} for z < 0, [tau-1, tau] at 0.
 __device__ __forceinline__ double dist_pinball(double t, double z, double tau) {
   if (z > 0.0) return fabs(t - tau);

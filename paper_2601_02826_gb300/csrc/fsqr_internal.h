@@ -9,7 +9,8 @@
 
 namespace fsqr {
 
-constexpr int kMaxNB = 8;          // fits advanced together per X pass
+constexpr int kMaxNB = 8;          // fits advanced together per X pass (narrow kernels)
+constexpr int kWideMax = 32;       // slots of a wide group (k_wide.cu)
 constexpr int kAThreads = 256;     // column kernel: 8 warps
 constexpr int kAWarps = kAThreads / 32;
 constexpr int kACols = 4;          // columns register-blocked per warp
@@ -37,6 +38,12 @@ struct Dsg {
   const double *cov;
   const double *a;
   const double *b;
+  // missing genotype entries (mean imputation, standardised value 0): per
+  // stored column s the sample indices midx[mptr[s] .. mptr[s+1]), ascending;
+  // both NULL when there are none. The stored codes read as 0 there, so every
+  // product of X~ subtracts b_j at those entries (the correction below).
+  const int64_t *mptr;
+  const int32_t *midx;
 };
 
 // State and parameters of a group of NB fits advanced together.
@@ -57,6 +64,7 @@ struct Fits {
   const double *inv_eta;  // G
   double tau[kMaxNB], lam[kMaxNB], lamnorm[kMaxNB];
   double mu, sigma, tol;
+  double ridge;           // elastic-net gamma: the quadratic weight of column j is ridge * omega_j
   int K, max_iter;
   // column-kernel outputs, one slot per CTA of the column kernel
   int gridA, T;
@@ -93,7 +101,13 @@ struct Fits {
   int64_t n4p;      // digit words per (fit, digit) row = npad / 4
   int32_t *digits;  // NB * D * n4p words, 4 samples per word
   double *scale;    // NB: quantisation scale 2^e
+  double *qcorr;    // npad*NB: - sum_j b_j beta_jb over the missing entries (i, j) of the
+                    // active stored columns, added and cleared by the vector update (NULL: none)
   double colbound;  // max_j a_j * sum_i |x_ij| over stored columns
+  // wide groups (k_wide.cu): per-slot parameters on the device, so that the
+  // host can refill a slot between replays of the captured iteration
+  const double *w_tau, *w_lam, *w_lamnorm;  // NB each
+  const int *w_k0;  // NB: iteration at which the slot's fit entered (its w^0)
 };
 
 // ---- launchers (kernels.cu) -------------------------------------------------
@@ -133,6 +147,28 @@ cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, c
                           const uint8_t *dgt, const TcSchedule &sc, int32_t *tail_part,
                           unsigned *tail_tick, int *err, cudaStream_t s);
 cudaError_t launch_tile_x(const Dsg &X, uint8_t *xt, int64_t nk, cudaStream_t s);
+
+// Wide groups (k_wide.cu), NB in {16, 32} slots. Digit matrix: 8 NB rows x
+// npad E4M3 bytes (tiled as for k_quantize_tc); X~ beta weight tiles:
+// 11 NB rows x 128 bytes per block of 128 active positions.
+bool wide_ok(int NB);
+size_t wcol_smem(int NB, int T);
+size_t wxbeta_smem(int NB);
+int wide_rows(int NB);     // 8 NB
+int wide_xrows(int NB);    // 11 NB
+cudaError_t launch_wquant(int NB, const Fits &F, int off, uint8_t *dg, cudaStream_t s);
+cudaError_t launch_wcol(int NB, const Dsg &X, const Fits &F, int off, const uint8_t *xt, const uint8_t *dgt,
+                        int rounds, int *err, cudaStream_t s);
+cudaError_t launch_wcheck(int NB, const Fits &F, int off, cudaStream_t s);
+// fuse = 1: X~ beta^{k+1} and the vector update of iterate k; fuse = 0 with
+// beta_in: the integer partials of X~ beta_in only (start of a solve).
+cudaError_t launch_wxbeta(int NB, const Dsg &X, const Fits &F, int off, int fuse, const double *beta_in,
+                          int *scol, uint8_t *wtile, int *err, int num_sms, cudaStream_t s);
+// Stop-test and quantisation partials of the current iterate of the slots
+// with mask[b] != 0, into tot_c[par] (a fit entering its slot).
+cudaError_t launch_slot_init(int NB, const Fits &F, int par, const int *mask, cudaStream_t s);
+cudaError_t launch_resid_slot(const double *xb, const double *z, const double *y, int64_t n, double *r, int slot,
+                              int NB, cudaStream_t s);
 // fuse = 1: the same launch also runs the vector update (k_vec) of the
 // iterate; fuse = 0: it leaves the integer partials for k_vec.
 cudaError_t launch_xbeta_tc(int NB, const Dsg &X, const Fits &F, int off, int fuse, const double *beta_in,
@@ -191,12 +227,35 @@ cudaError_t launch_min_omega(const double *omega, int64_t P, double *out, cudaSt
 cudaError_t launch_summary(int NB, int nb, int64_t n, int64_t P, const double *y,
                            const double *z, const double *r, const double *beta,
                            const double *omega, const double *taus, const double *lams,
-                           const double *s_chk, const double *tc, double *out, cudaStream_t s);
+                           const double *s_chk, const double *tc, double ridge, double *out, cudaStream_t s);
 cudaError_t launch_kkt_given(int64_t n, int64_t P, const double *y, const double *xb,
                              const double *z, const double *theta, const double *s,
                              const double *beta, const double *omega, double tau, double lam,
                              double *out, cudaStream_t st);
 cudaError_t launch_back_transform(const Dsg &X, const double *beta, int B, double *out,
                                   cudaStream_t s);
+cudaError_t launch_path_stats(const double *q, const double *y, const double *taus, int64_t n, const double *beta,
+                              int64_t P, int B, double *out, cudaStream_t s);
+cudaError_t launch_coverage(const double *qlo, const double *qhi, const double *y, int64_t n, double *out,
+                            cudaStream_t s);
+// Missing genotype entries (k_setup.cu): counts per stored column, the
+// column-major index lists, and an int8 copy with the missing codes set to 0.
+cudaError_t launch_miss_count(const Dsg &X, int *cnt, cudaStream_t s);
+cudaError_t launch_miss_fill(const Dsg &X, const int64_t *mptr, int32_t *midx, cudaStream_t s);
+cudaError_t launch_sanitize_int8(const Dsg &X, uint8_t *dst, cudaStream_t s);
+// u[g*npad + i] -= b_j v_j for the missing entries (i, j) of block g's stored
+// columns (the power method's X~_g v).
+cudaError_t launch_miss_xv(const Dsg &X, const double *v, const int64_t *block_ptr, int G, double *u,
+                           int64_t npad, cudaStream_t s);
+// qcorr[i*NB + b] -= b_j beta_jb over the missing entries of the active stored
+// columns (listed by the column pass), beta = beta_in or beta^{k+1}.
+cudaError_t launch_miss_xb(int NB, const Dsg &X, const Fits &F, int off, const double *beta_in, cudaStream_t s);
+cudaError_t launch_gather_cols(const uint8_t *src, int64_t ld, const int32_t *sel, int64_t nsel, uint8_t *dst,
+                               cudaStream_t s);
+cudaError_t launch_index_copy(const double *src, int64_t lds, const int32_t *idx, int64_t m, int nb, double *dst,
+                              int64_t ldd, int scatter, cudaStream_t s);
+cudaError_t launch_wait_selftest(long long budget, int arrive, int *err, int *ok, cudaStream_t s);
+cudaError_t launch_lla_weights(const double *src, const double *omega, int64_t P, double lam, double a, int type,
+                               double scale, double *out, cudaStream_t s);
 
 }  // namespace fsqr

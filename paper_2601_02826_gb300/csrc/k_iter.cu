@@ -342,11 +342,15 @@ __global__ void __launch_bounds__(kAThreads, ((D > 0 && NB * D <= 12) ? 2 : 1))
     bool act = false;
     if (lane_has && jq < j1) {
       const double aj = __ldg(X.a + jq), bj = __ldg(X.b + jq);
+      // mean imputation: the missing entries of a stored column read as 0,
+      // so their share b_j v_i of the constant part is taken back out
       if (MODE == A_XT) {
-        s_out[jq * NB + myb] = aj * mydot + bj * sS[myb];
+        const double mc = jq > X.c ? miss_dot(X, jq - 1 - X.c, vb, NB, myb) : 0.0;
+        s_out[jq * NB + myb] = aj * mydot + bj * (sS[myb] - mc);
       } else if (MODE == A_XT_BLOCK) {
         const int g = block_of(F.block_ptr, F.G, jq);
-        s_out[jq] = aj * mydot + bj * __ldg(vsum + g);
+        const double mc = jq > X.c ? miss_dot(X, jq - 1 - X.c, vec + (int64_t)g * F.npad, 1, 0) : 0.0;
+        s_out[jq] = aj * mydot + bj * (__ldg(vsum + g) - mc);
       } else if (MODE == A_LIST) {
         const double bv = bcur[jq * NB + myb];
         if (!sIdle[myb]) {
@@ -355,14 +359,19 @@ __global__ void __launch_bounds__(kAThreads, ((D > 0 && NB * D <= 12) ? 2 : 1))
           if (jq > X.c) wml = fmax(wml, fabs(aj * bv));
         }
       } else {  // A_PROX
-        const double s = aj * mydot + bj * sS[myb];
-        const double lamj = F.lam[myb] * __ldg(F.omega + jq);
+        const double mc = jq > X.c ? miss_dot(X, jq - 1 - X.c, vb, NB, myb) : 0.0;
+        const double s = aj * mydot + bj * (sS[myb] - mc);
+        const double om = __ldg(F.omega + jq);
+        const double lamj = F.lam[myb] * om;
+        const double gj = F.ridge * om;  // elastic-net quadratic weight (0: weighted l1)
         const double bo = bcur[jq * NB + myb];
         if (!sIdle[myb]) {
-          if (jq >= 1) rbl = fmax(rbl, dist_l1(s, lamj, bo));
+          if (jq >= 1) rbl = fmax(rbl, dist_l1(gj == 0.0 ? s : s - gj * bo, lamj, bo));
           const int g = block_of(F.block_ptr, F.G, jq);
-          const double eta = __ldg(F.eta + g), ie = __ldg(F.inv_eta + g);
+          const double eta = __ldg(F.eta + g);
+          const double ie = gj == 0.0 ? __ldg(F.inv_eta + g) : 1.0 / (eta + gj);
           // eq. beta_update: (1/eta)[(eta b + s - lam)_+ - (-eta b - s - lam)_+]
+          // (1/(eta + gamma_j) with the elastic-net term)
           const double av = eta * bo + s;
           const double bn = (fmax(av - lamj, 0.0) - fmax(-av - lamj, 0.0)) * ie;
           bnxt[jq * NB + myb] = bn;
@@ -651,7 +660,7 @@ __global__ void __launch_bounds__(256, 2)
       const int slot = t / NB, b = t - slot * NB;
       const int j = gcol[slot];
       long long W = 0;
-      if (j >= 0) W = __double2ll_rn(__ldg(X.a + j) * beta[(int64_t)j * NB + b] * sInv[b]);
+      if (j >= 0) W = fixed_point(__ldg(X.a + j) * beta[(int64_t)j * NB + b] * sInv[b]);
       int dig[kDWMax];
 #pragma unroll
       for (int d = DW - 1; d >= 1; --d) {
@@ -781,7 +790,7 @@ __global__ void __launch_bounds__(256) k_quantize(Fits F, int off) {
   const int64_t i = g - (int64_t)b * rows;
   const bool ok = b < NB;
   long long Xq = 0;
-  if (ok) Xq = __double2ll_rn(F.theta[i * NB + b] * sInv[b]);
+  if (ok) Xq = fixed_point(F.theta[i * NB + b] * sInv[b]);
   int dig[6];
 #pragma unroll
   for (int d = 5; d >= 0; --d) {
@@ -848,7 +857,9 @@ __global__ void __launch_bounds__(32) k_check(Fits F, int off) {
   const double R_b = (rb + bound) / F.lamnorm[b];
   const double R_1 = fabs(tc[2]);
   const double kkt = fmax(fmax(R_p, R_z), fmax(R_b, R_1));
-  const bool bad = !(kkt == kkt) || isinf(kkt);
+  // fmax drops a NaN operand, so each residual is tested: a NaN iterate
+  // reaches at least the sum of theta behind R_1
+  const bool bad = isnan(R_p) || isnan(R_z) || isnan(R_b) || isnan(R_1) || isinf(kkt);
   double *rep = F.report + b * kReport;
   rep[0] = kkt; rep[1] = R_p; rep[2] = R_z; rep[3] = R_b; rep[4] = R_1;
   rep[6] = bound / F.lamnorm[b];
@@ -943,6 +954,12 @@ __global__ void __launch_bounds__(kCThreads) k_vec(Dsg X, Fits F, int off, int i
     }
     const double yi = __ldg(F.y + i);
     const double nmu = (double)nrows * F.mu;
+    if (F.qcorr)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        xb[b] += F.qcorr[i * NB + b];
+        F.qcorr[i * NB + b] = 0.0;
+      }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       if (!run[b]) continue;
@@ -1011,6 +1028,10 @@ __global__ void k_gather_xb(Fits F, double *out, int64_t ldo, int nb, int64_t n)
   const int S = F.meta_i[0];
   double xb = F.meta_d[b];
   for (int sp = 0; sp < S; ++sp) xb += F.xb_part[((int64_t)sp * F.npad + i) * NB + b];
+  if (F.qcorr) {
+    xb += F.qcorr[i * NB + b];
+    F.qcorr[i * NB + b] = 0.0;
+  }
   out[(int64_t)b * ldo + i] = xb;
 }
 
@@ -1072,6 +1093,55 @@ int col_pass_occupancy(int NB, int mixed, int D, size_t smem) {
     case 8: return occ_nb<8>(mixed, D, smem);
     default: return 0;
   }
+}
+
+}  // namespace fsqr
+
+namespace fsqr {
+
+// Mean imputation in X~ beta: a missing entry (i, j) of a stored column
+// reads as code 0, which the slope/constant split turns into b_j; so
+// qcorr[i*NB + b] -= b_j beta_jb for the missing samples of every active
+// stored column (the active list of the column pass). Warps stride over the
+// active positions; atomic FP64 adds (the few corrections of one sample are
+// added in no fixed order).
+__global__ void __launch_bounds__(256) k_miss_xb(Dsg X, Fits F, int NB, int off, const double *__restrict__ beta_in) {
+  const double *beta = beta_in;
+  if (beta == nullptr) {
+    const int k = *F.it_base + off;
+    beta = F.beta[(k & 1) ^ 1];
+  }
+  const int gA = F.gridA;
+  const int A = __ldcg(F.a_pre + gA);
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t a = w0; a < A; a += nw) {
+    int lo = 0, hi = gA;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldcg(F.a_pre + mid) <= a) lo = mid; else hi = mid;
+    }
+    const int64_t j = F.a_list[(int64_t)lo * F.T + (a - __ldcg(F.a_pre + lo))];
+    if (j <= X.c) continue;  // intercept and covariates have no missing entries
+    const int64_t s = j - 1 - X.c;
+    const double bj = X.b[j];
+    const int64_t e0 = X.mptr[s], e1 = X.mptr[s + 1];
+    for (int b = 0; b < NB; ++b) {
+      const double c = -bj * beta[j * NB + b];
+      if (c == 0.0) continue;
+      for (int64_t e = e0 + lane; e < e1; e += 32) atomicAdd(F.qcorr + (int64_t)X.midx[e] * NB + b, c);
+    }
+  }
+}
+
+cudaError_t launch_miss_xb(int NB, const Dsg &X, const Fits &F, int off, const double *beta_in, cudaStream_t s) {
+  if (X.mptr == nullptr || F.qcorr == nullptr) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_miss_xb<<<std::max(1, sms) * 4, 256, 0, s>>>(X, F, NB, off, beta_in);
+  return cudaGetLastError();
 }
 
 }  // namespace fsqr

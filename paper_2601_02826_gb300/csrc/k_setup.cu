@@ -536,7 +536,7 @@ cudaError_t launch_min_omega(const double *omega, int64_t P, double *out, cudaSt
 
 // Per fit b (one CTA): out[b*8 + ...] = {loss, penalty, active, alpha, y.tc}
 //   loss    = (1/n) sum_i rho_tau(z_i - r_i)   (z - r = y - X~ beta)
-//   penalty = sum_j lam_b omega_j |beta_j|
+//   penalty = sum_j lam_b omega_j |beta_j| (+ ridge/2 sum_j omega_j beta_j^2)
 //   active  = #{j >= 1 : beta_j != 0}
 //   alpha   = min(1, min_{j>=1} lam_j / |s_j|) for s = X~^T theta_check (if s)
 //   y.tc    = sum_i y_i theta_check_i (if tc)
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(512) k_summary(int NB, int64_t n, int64_t P, c
                                                  const double *z, const double *r,
                                                  const double *beta, const double *omega,
                                                  const double *taus, const double *lams,
-                                                 const double *s_chk, const double *tc,
+                                                 const double *s_chk, const double *tc, double ridge,
                                                  double *out) {
   __shared__ double sh[512];
   const int b = blockIdx.x;
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(512) k_summary(int NB, int64_t n, int64_t P, c
   for (int64_t j = threadIdx.x; j < P; j += blockDim.x) {
     const double bj = beta[j * NB + b];
     const double lj = lam * omega[j];
-    pen += lj * fabs(bj);
+    pen += lj * fabs(bj) + 0.5 * ridge * omega[j] * bj * bj;
     if (j >= 1 && bj != 0.0) act += 1.0;
     if (s_chk && j >= 1) {
       const double sa = fabs(s_chk[j * NB + b]);
@@ -586,8 +586,8 @@ __global__ void __launch_bounds__(512) k_summary(int NB, int64_t n, int64_t P, c
 cudaError_t launch_summary(int NB, int nb, int64_t n, int64_t P, const double *y, const double *z,
                            const double *r, const double *beta, const double *omega,
                            const double *taus, const double *lams, const double *s_chk,
-                           const double *tc, double *out, cudaStream_t s) {
-  k_summary<<<nb, 512, 0, s>>>(NB, n, P, y, z, r, beta, omega, taus, lams, s_chk, tc, out);
+                           const double *tc, double ridge, double *out, cudaStream_t s) {
+  k_summary<<<nb, 512, 0, s>>>(NB, n, P, y, z, r, beta, omega, taus, lams, s_chk, tc, ridge, out);
   return cudaGetLastError();
 }
 
@@ -661,6 +661,257 @@ cudaError_t launch_back_transform(const Dsg &X, const double *beta, int B, doubl
                                   cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   k_back_transform<<<B, 512, 0, s>>>(X, beta, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fsqr
+
+namespace fsqr {
+
+// Penalty weights of an LLA step (Section 6, Algorithm 2), out[0] = 0 and
+// for j >= 1:
+//   type FSQR_PEN_SCAD: omega_j p'(|src_j|) scale, p' of eq. scad (a > 2)
+//   type FSQR_PEN_MCP:  omega_j p'(|src_j|) scale, p' of eq. mcp  (a > 1)
+//   type 0:             omega_j lam scale (the weighted-l1 weights)
+//   type -1:            src_j scale
+__global__ void k_lla_weights(const double *src, const double *omega, int64_t P, double lam, double a, int type,
+                              double scale, double *out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P) return;
+  if (j == 0) { out[0] = 0.0; return; }
+  double v;
+  if (type == FSQR_PEN_SCAD || type == FSQR_PEN_MCP) {
+    const double t = fabs(src[j]);
+    double d;
+    if (type == FSQR_PEN_SCAD) d = (t <= lam) ? lam : ((t < a * lam) ? (a * lam - t) / (a - 1.0) : 0.0);
+    else d = (t <= a * lam) ? lam - t / a : 0.0;
+    v = omega[j] * d * scale;
+  } else if (type == 0) {
+    v = omega[j] * lam * scale;
+  } else {
+    v = src[j] * scale;
+  }
+  out[j] = v;
+}
+
+cudaError_t launch_lla_weights(const double *src, const double *omega, int64_t P, double lam, double a, int type,
+                               double scale, double *out, cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  k_lla_weights<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(src, omega, P, lam, a, type, scale, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fsqr
+
+namespace fsqr {
+
+// Model selection along a path (Section 7), one CTA per fit b:
+//   out[2b]     = sum_i rho_{tau_b}(y_i - q_{b,i})   (q = X~ beta_b, row b*n)
+//   out[2b + 1] = #{j >= 1 : beta_{b,j} != 0}
+__global__ void __launch_bounds__(512) k_path_stats(const double *q, const double *y, const double *taus, int64_t n,
+                                                    const double *beta, int64_t P, double *out) {
+  __shared__ double sh[512];
+  const int b = blockIdx.x;
+  const double tau = taus[b];
+  double loss = 0.0, act = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double u = y[i] - q[(int64_t)b * n + i];
+    loss += (tau - (u < 0.0 ? 1.0 : 0.0)) * u;
+  }
+  for (int64_t j = 1 + threadIdx.x; j < P; j += blockDim.x) act += (beta[(int64_t)b * P + j] != 0.0) ? 1.0 : 0.0;
+  loss = block_sum(loss, sh);
+  act = block_sum(act, sh);
+  if (threadIdx.x == 0) {
+    out[2 * b] = loss;
+    out[2 * b + 1] = act;
+  }
+}
+
+cudaError_t launch_path_stats(const double *q, const double *y, const double *taus, int64_t n, const double *beta,
+                              int64_t P, int B, double *out, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  k_path_stats<<<B, 512, 0, s>>>(q, y, taus, n, beta, P, out);
+  return cudaGetLastError();
+}
+
+// Prediction intervals [q_lo, q_hi] (Section 7.1): out = {number of samples
+// with q_lo <= y <= q_hi and q_lo <= q_hi, sum of q_hi - q_lo, number of
+// crossings q_lo > q_hi} (one CTA, fixed-order reduction).
+__global__ void __launch_bounds__(1024) k_coverage(const double *qlo, const double *qhi, const double *y, int64_t n,
+                                                   double *out) {
+  __shared__ double sh[1024];
+  double cov = 0.0, wid = 0.0, cr = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double lo = qlo[i], hi = qhi[i], yi = y[i];
+    cov += (lo <= hi && lo <= yi && yi <= hi) ? 1.0 : 0.0;
+    wid += hi - lo;
+    cr += (lo > hi) ? 1.0 : 0.0;
+  }
+  cov = block_sum(cov, sh);
+  wid = block_sum(wid, sh);
+  cr = block_sum(cr, sh);
+  if (threadIdx.x == 0) {
+    out[0] = cov;
+    out[1] = wid;
+    out[2] = cr;
+  }
+}
+
+cudaError_t launch_coverage(const double *qlo, const double *qhi, const double *y, int64_t n, double *out,
+                            cudaStream_t s) {
+  k_coverage<<<1, 1024, 0, s>>>(qlo, qhi, y, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fsqr
+
+namespace fsqr {
+
+// ------------------------------------------- missing genotype entries
+// (mean imputation of Section 7.2: a missing entry takes the column mean,
+// i.e. standardised value 0)
+
+__device__ __forceinline__ bool is_missing(const Dsg &X, const uint8_t *col, int64_t i) {
+  if (X.fmt == FSQR_INT8) return col[i] > 2u;
+  if (X.fmt == FSQR_2BIT) return ((col[i >> 2] >> (2 * (i & 3))) & 3u) == 3u;
+  return false;
+}
+
+// One warp per stored column: cnt[s] = number of missing samples.
+__global__ void k_miss_count(Dsg X, int *cnt) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= X.p) return;
+  const uint8_t *col = X.geno + s * X.ld;
+  int c = 0;
+  for (int64_t i = lane; i < X.n; i += 32) c += is_missing(X, col, i) ? 1 : 0;
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) cnt[s] = c;
+}
+
+cudaError_t launch_miss_count(const Dsg &X, int *cnt, cudaStream_t s) {
+  if (X.p == 0) return cudaSuccess;
+  const int64_t threads = X.p * 32;
+  k_miss_count<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(X, cnt);
+  return cudaGetLastError();
+}
+
+// One warp per stored column: the missing samples in ascending order.
+__global__ void k_miss_fill(Dsg X, const int64_t *mptr, int32_t *midx) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= X.p) return;
+  const uint8_t *col = X.geno + s * X.ld;
+  int64_t pos = mptr[s];
+  for (int64_t i0 = 0; i0 < X.n; i0 += 32) {
+    const int64_t i = i0 + lane;
+    const bool m = i < X.n && is_missing(X, col, i);
+    const unsigned bal = __ballot_sync(0xffffffffu, m);
+    if (m) midx[pos + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+    pos += __popc(bal);
+  }
+}
+
+cudaError_t launch_miss_fill(const Dsg &X, const int64_t *mptr, int32_t *midx, cudaStream_t s) {
+  if (X.p == 0) return cudaSuccess;
+  const int64_t threads = X.p * 32;
+  k_miss_fill<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(X, mptr, midx);
+  return cudaGetLastError();
+}
+
+// dst: a copy of the int8 stored columns (same ld) with missing codes set to 0.
+__global__ void k_sanitize_int8(Dsg X, uint8_t *dst) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte chunk
+  const int64_t per = X.ld / 16;
+  if (g >= X.p * per) return;
+  const uint4 v = reinterpret_cast<const uint4 *>(X.geno)[g];
+  uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint32_t byte = (w[q] >> (8 * t)) & 0xffu;
+      o |= (byte <= 2u ? byte : 0u) << (8 * t);
+    }
+    w[q] = o;
+  }
+  reinterpret_cast<uint4 *>(dst)[g] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+cudaError_t launch_sanitize_int8(const Dsg &X, uint8_t *dst, cudaStream_t s) {
+  const int64_t chunks = X.p * (X.ld / 16);
+  if (chunks == 0) return cudaSuccess;
+  k_sanitize_int8<<<(unsigned)((chunks + 255) / 256), 256, 0, s>>>(X, dst);
+  return cudaGetLastError();
+}
+
+// One warp per stored column j of block g: u[g*npad + i] -= b_j v_j at its
+// missing samples (atomic FP64 adds: the order of the few corrections per
+// sample is not fixed).
+__global__ void k_miss_xv(Dsg X, const double *v, const int64_t *block_ptr, int G, double *u, int64_t npad) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= X.p) return;
+  const int64_t j = 1 + X.c + s;
+  const double c = -X.b[j] * v[j];
+  if (c == 0.0) return;
+  int lo = 0, hi = G;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (block_ptr[mid] <= j) lo = mid; else hi = mid;
+  }
+  double *ug = u + (int64_t)lo * npad;
+  for (int64_t e = X.mptr[s] + lane; e < X.mptr[s + 1]; e += 32) atomicAdd(ug + X.midx[e], c);
+}
+
+cudaError_t launch_miss_xv(const Dsg &X, const double *v, const int64_t *block_ptr, int G, double *u,
+                           int64_t npad, cudaStream_t s) {
+  if (X.p == 0 || X.mptr == nullptr) return cudaSuccess;
+  const int64_t threads = X.p * 32;
+  k_miss_xv<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(X, v, block_ptr, G, u, npad);
+  return cudaGetLastError();
+}
+
+}  // namespace fsqr
+
+namespace fsqr {
+
+// ------------------------------------------------ screening (strong rule)
+
+// dst column q = src column sel[q] (ld bytes each, 16-byte chunks).
+__global__ void k_gather_cols(const uint8_t *src, int64_t ld, const int32_t *sel, int64_t nsel, uint8_t *dst) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = ld / 16;
+  if (g >= nsel * per) return;
+  const int64_t q = g / per, c = g - q * per;
+  reinterpret_cast<uint4 *>(dst + q * ld)[c] = reinterpret_cast<const uint4 *>(src + (int64_t)sel[q] * ld)[c];
+}
+
+cudaError_t launch_gather_cols(const uint8_t *src, int64_t ld, const int32_t *sel, int64_t nsel, uint8_t *dst,
+                               cudaStream_t s) {
+  const int64_t chunks = nsel * (ld / 16);
+  if (chunks == 0) return cudaSuccess;
+  k_gather_cols<<<(unsigned)((chunks + 255) / 256), 256, 0, s>>>(src, ld, sel, nsel, dst);
+  return cudaGetLastError();
+}
+
+// dst[b*ldd + q] = src[b*lds + idx[q]] for b < nb, q < m (gather) or, with
+// scatter = 1, dst[b*ldd + idx[q]] = src[b*lds + q].
+__global__ void k_index_copy(const double *src, int64_t lds, const int32_t *idx, int64_t m, int nb, double *dst,
+                             int64_t ldd, int scatter) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= m * nb) return;
+  const int b = (int)(g / m);
+  const int64_t q = g - (int64_t)b * m;
+  if (scatter) dst[b * ldd + idx[q]] = src[b * lds + q];
+  else dst[b * ldd + q] = src[b * lds + idx[q]];
+}
+
+cudaError_t launch_index_copy(const double *src, int64_t lds, const int32_t *idx, int64_t m, int nb, double *dst,
+                              int64_t ldd, int scatter, cudaStream_t s) {
+  if (m * nb == 0) return cudaSuccess;
+  k_index_copy<<<(unsigned)((m * nb + 255) / 256), 256, 0, s>>>(src, lds, idx, m, nb, dst, ldd, scatter);
   return cudaGetLastError();
 }
 

@@ -89,15 +89,20 @@ __device__ __forceinline__ bool col_update(const Dsg &X, const Fits &F, int64_t 
                                            const double *bcur, double *bnxt, double (&rbl)[NB],
                                            double (&ctl)[NB], double (&wml)[NB], double aj, double bj,
                                            double om, const double (&bo)[NB], double eta, double ie) {
+  // ie is 1/eta_g, or 1/(eta_g + gamma_j) with the elastic-net term
   const double dscale = ldexp(1.0, -4 * D);
+  const double gj = F.ridge * om;  // elastic-net quadratic weight (0: weighted l1)
+  if (gj != 0.0) ie = 1.0 / (eta + gj);
   bool act = false;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const double dot = (double)V[b] * (sScale[b] * dscale);
-    const double s = aj * dot + bj * sS[b];
+    // mean imputation: missing entries read as 0, so their b_j theta_i is taken back out
+    const double mc = X.mptr ? miss_dot(X, j - 1 - X.c, F.theta, NB, b) : 0.0;
+    const double s = aj * dot + bj * (sS[b] - mc);
     const double lamj = F.lam[b] * om;
     if (!sIdle[b]) {
-      rbl[b] = fmax(rbl[b], dist_l1_tc(s, lamj, bo[b]));
+      rbl[b] = fmax(rbl[b], dist_l1_tc(gj == 0.0 ? s : s - gj * bo[b], lamj, bo[b]));
       const double av = eta * bo[b] + s;
       const double bn = (fmax(av - lamj, 0.0) - fmax(-av - lamj, 0.0)) * ie;
       bnxt[j * NB + b] = bn;
@@ -253,7 +258,8 @@ __global__ void __launch_bounds__(256, 1)
       if (dl == 0) {
         const double aj = X.a[j], bj = X.b[j];
         const int g = block_of_tc(F.block_ptr, F.G, j);
-        const double eta = F.eta[g], ie = F.inv_eta[g];
+        const double gj = F.ridge * F.omega[j];
+        const double eta = F.eta[g], ie = gj == 0.0 ? F.inv_eta[g] : 1.0 / (F.eta[g] + gj);
         bool act = false;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(256, 1)
           const double s = aj * (s_dot[0][b] + s_dot[1][b]) + bj * sS[b];
           const double lamj = F.lam[b] * F.omega[j];
           const double bo = bcur[j * NB + b];
-          if (j >= 1) rbl[b] = fmax(rbl[b], dist_l1_tc(s, lamj, bo));
+          if (j >= 1) rbl[b] = fmax(rbl[b], dist_l1_tc(gj == 0.0 ? s : s - gj * bo, lamj, bo));
           const double av = eta * bo + s;
           const double bn = (fmax(av - lamj, 0.0) - fmax(-av - lamj, 0.0)) * ie;
           bnxt[j * NB + b] = bn;
@@ -485,7 +491,7 @@ __global__ void __launch_bounds__(256) k_quantize_tc(Fits F, int off, uint8_t *d
   const int b = (int)(g / F.npad);
   const int64_t i = g - (int64_t)b * F.npad;
   if (b >= NB) return;
-  long long Xq = __double2ll_rn(F.theta[i * NB + b] * sInv[b]);
+  long long Xq = fixed_point(F.theta[i * NB + b] * sInv[b]);
   int dig[D];
 #pragma unroll
   for (int d = D - 1; d >= 1; --d) {
@@ -625,7 +631,7 @@ __global__ void __launch_bounds__(128)
     const double aj = (j >= 0) ? __ldg(X.a + j) : 0.0;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      long long W = (j >= 0) ? __double2ll_rn(aj * beta[(int64_t)j * NB + b] * sInv[b]) : 0;
+      long long W = (j >= 0) ? fixed_point(aj * beta[(int64_t)j * NB + b] * sInv[b]) : 0;
       int dig[DWD];
 #pragma unroll
       for (int d = DWD - 1; d >= 1; --d) {
@@ -861,9 +867,14 @@ __global__ void __launch_bounds__(128)
     const double nmu = (double)F.n * F.mu;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
+      double qc = 0.0;
+      if (F.qcorr) {
+        qc = F.qcorr[i * NB + b];
+        F.qcorr[i * NB + b] = 0.0;
+      }
       if (!run[b]) continue;
       const double unit = F.meta_d[kMaxNB + b] * F.xb_unit;
-      const double q = F.meta_d[b] + (double)V[b] * unit + cv[b];
+      const double q = F.meta_d[b] + (double)V[b] * unit + cv[b] + qc;
       row_update(F, i * NB + b, F.tau[b], nmu, (double)F.n, q, (double)A * unit, yi, zo[b], th[b], ro[b], p[b]);
     }
   }

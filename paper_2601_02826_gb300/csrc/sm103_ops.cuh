@@ -58,18 +58,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Waits for the phase with the given parity; returns false (and records
-// code in *err) when the budget runs out or another role already failed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+// code in *err) when `budget` cycles run out or another role already failed.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, int *err, int code, long long budget) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*(volatile int *)err != 0) return false;
-    if (clock64() - t0 > kWaitBudget) {
+    if (clock64() - t0 > budget) {
       atomicCAS(err, 0, code);
       return false;
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+  return mbar_wait_for(bar, parity, err, code, kWaitBudget);
 }
 
 // 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16),

@@ -19,6 +19,7 @@ OK, EINVAL, ENOCONV, ETIMEOUT, ENUMERIC, ECUDA, ENOMEM = range(7)
 DENSE_F64, INT8, TWOBIT = 0, 1, 2
 FP64, MIXED, MIXED_SIMT = 0, 1, 2
 WARM_NONE, WARM_GIVEN, WARM_PATH = 0, 1, 2
+PEN_SCAD, PEN_MCP = 1, 2
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOCONV", 3: "ETIMEOUT", 4: "ENUMERIC", 5: "ECUDA", 6: "ENOMEM"}
 
@@ -35,7 +36,8 @@ class Opts(C.Structure):
                 ("mu", C.c_double), ("eta", C.POINTER(C.c_double)), ("eta_margin", C.c_double),
                 ("power_iters", C.c_int32), ("power_tol", C.c_double), ("precision", C.c_int32),
                 ("warm", C.c_int32), ("digits", C.c_int32), ("max_group", C.c_int32),
-                ("timeout_ms", C.c_int64), ("warm_params", C.c_void_p)]
+                ("timeout_ms", C.c_int64), ("warm_params", C.c_void_p), ("ridge", C.c_double),
+                ("screen", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -54,7 +56,8 @@ class Profile(C.Structure):
     _fields_ = [("col_samples", C.c_int64), ("col_ms", C.c_double), ("xb_samples", C.c_int64),
                 ("xb_ms", C.c_double), ("vec_samples", C.c_int64), ("vec_ms", C.c_double),
                 ("iterations", C.c_int64), ("kernel_launches", C.c_int64), ("col_bytes", C.c_int64),
-                ("tuned_group", C.c_int64)]
+                ("tuned_group", C.c_int64), ("tc_groups", C.c_int64), ("simt_groups", C.c_int64),
+                ("wide_groups", C.c_int64), ("screen_kept", C.c_int64), ("screen_total", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -62,8 +65,8 @@ class Profile(C.Structure):
 
 EXPORTS = ["fsqr_version", "fsqr_opts_default", "fsqr_create", "fsqr_destroy", "fsqr_last_error",
            "fsqr_col_stats", "fsqr_lambda_max", "fsqr_eta", "fsqr_fit", "fsqr_fit_batch",
-           "fsqr_fit_batch_host", "fsqr_kkt", "fsqr_predict", "fsqr_back_transform",
-           "fsqr_profile_enable", "fsqr_profile_get", "fsqr_profile_reset",
+           "fsqr_fit_batch_host", "fsqr_fit_lla", "fsqr_path_stats", "fsqr_interval_coverage", "fsqr_kkt", "fsqr_predict", "fsqr_back_transform",
+           "fsqr_profile_enable", "fsqr_profile_get", "fsqr_profile_reset", "fsqr_wait_selftest",
            "fsqr_lambda_max_noalloc", "fsqr_mlp_param_count", "fsqr_mlp_init", "fsqr_mlp_forward",
            "fsqr_mlp_grad", "fsqr_mlp_train", "fsqr_warm_features", "fsqr_warm_start"]
 
@@ -100,10 +103,14 @@ def load(path: str | None = None):
     L.fsqr_fit.argtypes = [vp, pD, vp, dbl, dbl, vp, pi64, i32, pO, vp, vp, vp, pI]
     L.fsqr_fit_batch.argtypes = [vp, pD, vp, i32, pd, i32, pd, vp, pi64, i32, pO, vp, vp, vp, pI]
     L.fsqr_fit_batch_host.argtypes = [vp, pD, vp, i32, pd, i32, pd, vp, pi64, i32, pO, vp, vp, vp, pI]
+    L.fsqr_fit_lla.argtypes = [vp, pD, vp, dbl, dbl, vp, pi64, i32, i32, dbl, i32, pO, vp, vp, vp, vp, pI]
+    L.fsqr_path_stats.argtypes = [vp, pD, vp, i32, pd, vp, pd, pi64, pd]
+    L.fsqr_interval_coverage.argtypes = [vp, pD, vp, vp, vp, pd, pd, pi64]
     L.fsqr_kkt.argtypes = [vp, pD, vp, dbl, dbl, vp, dbl, vp, vp, vp, pI]
     L.fsqr_predict.argtypes = [vp, pD, vp, i32, vp]
     L.fsqr_back_transform.argtypes = [vp, pD, vp, i32, vp]
     L.fsqr_profile_enable.argtypes = [vp, i32]
+    L.fsqr_wait_selftest.argtypes = [vp, i64, i32, C.POINTER(C.c_int)]
     L.fsqr_profile_get.argtypes = [vp, C.POINTER(Profile)]
     L.fsqr_profile_reset.argtypes = [vp]
     u64, flt = C.c_uint64, C.c_float
@@ -264,6 +271,40 @@ class Context:
         self._check(rc, allowed)
         return rc, list(infos)
 
+    def fit_lla(self, d, y, tau, lam, omega, block_ptr, penalty, a, L, beta, z, theta, lam_out=None,
+                opts=None, allowed=(OK, ENOCONV, ETIMEOUT)):
+        """fsqr_fit_lla: L-step LLA for SCAD (PEN_SCAD) or MCP (PEN_MCP)."""
+        bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
+        G = len(bp) - 1
+        o, keep = self._opts(opts, G)
+        info = Info()
+        rc = self.L.fsqr_fit_lla(self.h, C.byref(d), _ptr(y), tau, lam, _ptr(omega),
+                                 bp.ctypes.data_as(C.POINTER(C.c_int64)), G, penalty, a, L, C.byref(o),
+                                 _ptr(beta), _ptr(z), _ptr(theta), _ptr(lam_out), C.byref(info))
+        self._check(rc, allowed)
+        return rc, info
+
+    def path_stats(self, d, y, taus, beta):
+        """fsqr_path_stats: (loss, active, hbic) of B fits (numpy arrays)."""
+        taus = np.ascontiguousarray(taus, dtype=np.float64)
+        B = len(taus)
+        loss, hb = np.zeros(B), np.zeros(B)
+        act = np.zeros(B, dtype=np.int64)
+        self._check(self.L.fsqr_path_stats(self.h, C.byref(d), _ptr(y), B,
+                                           taus.ctypes.data_as(C.POINTER(C.c_double)), _ptr(beta),
+                                           loss.ctypes.data_as(C.POINTER(C.c_double)),
+                                           act.ctypes.data_as(C.POINTER(C.c_int64)),
+                                           hb.ctypes.data_as(C.POINTER(C.c_double))))
+        return loss, act, hb
+
+    def interval_coverage(self, d, y, beta_lo, beta_hi):
+        """fsqr_interval_coverage: (coverage, mean width, crossings)."""
+        cov, wid = C.c_double(), C.c_double()
+        cr = C.c_int64()
+        self._check(self.L.fsqr_interval_coverage(self.h, C.byref(d), _ptr(y), _ptr(beta_lo), _ptr(beta_hi),
+                                                  C.byref(cov), C.byref(wid), C.byref(cr)))
+        return cov.value, wid.value, cr.value
+
     def kkt(self, d, y, tau, lam, omega, lam_norm, beta, z, theta) -> Info:
         info = Info()
         self._check(self.L.fsqr_kkt(self.h, C.byref(d), _ptr(y), tau, lam, _ptr(omega), lam_norm,
@@ -318,6 +359,13 @@ class Context:
         p = Profile()
         self.L.fsqr_profile_get(self.h, C.byref(p))
         return p
+
+    def wait_selftest(self, budget_cycles: int, arrive: bool):
+        """fsqr_wait_selftest: (status, wait_ok)."""
+        ok = C.c_int(0)
+        rc = self.L.fsqr_wait_selftest(self.h, budget_cycles, 1 if arrive else 0, C.byref(ok))
+        self._check(rc, (OK, ETIMEOUT))
+        return rc, ok.value
 
     def last_error(self) -> str:
         return self.L.fsqr_last_error(self.h).decode()

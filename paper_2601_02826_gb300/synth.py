@@ -14,6 +14,8 @@ scaled to the five workloads below:
   grid_int8       n=10,000, p=500,000    int8, ragged blocks U(5k,30k)
   warm_2bit       n=20,000, p=1,000,000  2-bit packed
   biobank_2bit    n=50,000, p=2,000,000  2-bit packed with AR(1) LD
+  paper_sparse    n=1,000,  p=2,000      the paper's sparse DGP (Section 7.1), dense FP64
+  paper_dense     n=10,000, p=20,000     the paper's dense DGP (Section 7.2), dense FP64
 
 Genotype storage is SNP-major (one SNP column = all samples, contiguous),
 padded to a 16-byte multiple per column:
@@ -297,6 +299,69 @@ def biobank_2bit(seed=None, n=50_000, p=2_000_000, c=10, blocks=("ragged", 5000,
     fr = list(np.geomspace(1.0, 0.01, 50))
     return geno_workload("biobank_2bit", n, p, c, FMT_2BIT, 500, 0.05, "t3", False, taus, fr, blocks,
                          SEED_BASE + 5 if seed is None else seed, ld_rho=0.8)
+
+
+def _ar1_gaussian(rng, n, p, rho=0.5):
+    """n draws of N(0, Sigma) with Sigma_ij = rho^|i-j| (a stationary AR(1) across the columns)."""
+    X = np.empty((p, n))
+    X[0] = rng.standard_normal(n)
+    b = math.sqrt(1.0 - rho * rho)
+    for j in range(1, p):
+        X[j] = rho * X[j - 1] + b * rng.standard_normal(n)
+    return X
+
+
+def paper_sparse(n=1000, p=2000, seed=None, G=5, tau=0.5):
+    """The sparse simulation design of the paper's Section 7.1 (eq. dgp_simulation):
+    X~ ~ N(0, Sigma), Sigma_ij = 0.5^|i-j|; X_1 = Phi(X~_1), X_j = X~_j otherwise;
+    Y = X_6 - X_20 + X_50 - X_100 + X_500 - X_1000 + X_p + 0.7 X_1 eps, eps ~ N(0, 1).
+    Dense FP64 storage, every omega_j = 1, G = 5 equal blocks. beta_true holds
+    the tau = 0.5 quantile coefficients (beta_1 = 0.7 Phi^{-1}(tau) in general)."""
+    from scipy.special import ndtr
+    rng = np.random.default_rng(SEED_BASE + 11 if seed is None else seed)
+    X = _ar1_gaussian(rng, n, p)
+    X[0] = ndtr(X[0])
+    beta = np.zeros(p)
+    for j, v in ((6, 1.0), (20, -1.0), (50, 1.0), (100, -1.0), (500, 1.0), (1000, -1.0), (p, 1.0)):
+        if j <= p:
+            beta[j - 1] += v
+    y = beta @ X + 0.7 * X[0] * rng.standard_normal(n)
+    P = 1 + p
+    omega = np.ones(P)
+    omega[0] = 0.0
+    ld = padded_ld(n, FMT_DENSE_F64)
+    Xs = np.zeros((p, ld // 8))
+    Xs[:, :n] = X
+    return Workload("paper_sparse", n, p, 0, FMT_DENSE_F64, Xs, ld, np.zeros((0, n)), y, [tau],
+                    equal_blocks(P, G), omega, [0.1], beta,
+                    recipe=f"Section 7.1 sparse DGP: AR(1) 0.5 Gaussian {n}x{p}, X_1 = Phi(.), "
+                           f"heteroscedastic 0.7 X_1 eps; G={G}")
+
+
+def paper_dense(n=10_000, p=20_000, seed=None, G=5, m1=500, m2=50, s1=0.3, s2=0.1):
+    """The dense simulation design of the paper's Section 7.2: the same AR(1)
+    design with X_j = Phi(X~_j) for m1 < j <= m1 + m2;
+    Y = sum_{j<=m1} a_j X_j + (sum_{m1<j<=m1+m2} |b_j| X_j) eps,
+    a_j ~ N(0, s1/m1), b_j ~ N(0, s2/m2), eps ~ N(0, 1)."""
+    from scipy.special import ndtr
+    rng = np.random.default_rng(SEED_BASE + 12 if seed is None else seed)
+    X = _ar1_gaussian(rng, n, p)
+    X[m1:m1 + m2] = ndtr(X[m1:m1 + m2])
+    a = rng.normal(0.0, math.sqrt(s1 / m1), m1)
+    b = rng.normal(0.0, math.sqrt(s2 / m2), m2)
+    y = a @ X[:m1] + (np.abs(b) @ X[m1:m1 + m2]) * rng.standard_normal(n)
+    beta = np.zeros(p)
+    beta[:m1] = a
+    P = 1 + p
+    omega = np.ones(P)
+    omega[0] = 0.0
+    ld = padded_ld(n, FMT_DENSE_F64)
+    Xs = np.zeros((p, ld // 8))
+    Xs[:, :n] = X
+    return Workload("paper_dense", n, p, 0, FMT_DENSE_F64, Xs, ld, np.zeros((0, n)), y, [0.1, 0.5, 0.9],
+                    equal_blocks(P, G), omega, [0.1], beta,
+                    recipe=f"Section 7.2 dense DGP: AR(1) 0.5 Gaussian {n}x{p}, {m1} effects N(0,{s1}/{m1}), "
+                           f"{m2} scale columns Phi(.); G={G}")
 
 
 def tiny_geno(seed, n, p, c=0, fmt=FMT_INT8, G=3, missing=0.0, taus=(0.5,), penalize_cov=True):

@@ -76,3 +76,9 @@ def test_create_fails_cleanly_without_a_device():
     L = fsqr.load()
     h = ctypes.c_void_p()
     assert L.fsqr_create(ctypes.byref(h), 0, None) != 0
+
+
+def test_header_declares_the_new_entry_points():
+    h = open(os.path.join(ROOT, "include", "fsqr.h")).read()
+    for name in ("fsqr_fit_lla", "fsqr_path_stats", "fsqr_interval_coverage", "fsqr_wait_selftest"):
+        assert name + "(" in h, name

@@ -349,7 +349,7 @@ def test_invalid_arguments_are_rejected_and_context_survives(ctx):
     bad = [
         dict(tau=0.0), dict(tau=1.0), dict(lam=-1.0), dict(bp=np.array([0, 5, 5, w.P])),
         dict(bp=np.array([0, w.P - 1])), dict(opts=dict(digits=9, precision=1)),
-        dict(opts=dict(check_every=0)), dict(opts=dict(max_group=9)),
+        dict(opts=dict(check_every=0)), dict(opts=dict(max_group=33)), dict(opts=dict(ridge=-1.0)),
     ]
     for case in bad:
         b, z, t = st()
@@ -369,13 +369,16 @@ def test_invalid_arguments_are_rejected_and_context_survives(ctx):
     assert ctx.lambda_max(dw.design, dw.y, 0.5, dw.omega) > 0
 
 
-def test_missing_genotypes_are_rejected_not_misread(ctx):
-    from paper_2601_02826_gb300 import fsqr
+def test_missing_genotypes_are_imputed_not_misread(ctx):
+    """Missing codes take the column mean (standardised value 0): lambda_max
+    of a design with 2 % missing entries matches the oracle's imputation."""
     w = synth.tiny_geno(106, 200, 100, missing=0.02)
     dw = _up(ctx, w)
-    with pytest.raises(fsqr.FsqrError) as e:
-        ctx.lambda_max(dw.design, dw.y, 0.5, dw.omega)
-    assert e.value.code == fsqr.EINVAL and "missing" in str(e.value)
+    d = O.build_design(O.decode_stored(w.geno, w.fmt, w.n), w.cov)
+    assert np.isnan(O.raw_columns(O.decode_stored(w.geno, w.fmt, w.n), w.cov)).any()
+    for tau in (0.3, 0.5):
+        assert ctx.lambda_max(dw.design, dw.y, tau, dw.omega) == pytest.approx(
+            O.lambda_max(d.Xt, w.y, tau, w.omega), rel=1e-10)
 
 
 def test_timeout_returns_valid_iterate(ctx):

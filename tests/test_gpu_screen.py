@@ -1,0 +1,89 @@
+"""Sequential strong-rule screening along the lambda path (opts.screen) on
+the GPU against the oracle: every screened fit meets the oracle's stop test
+on the FULL design, its objective matches the unscreened fit's, and the
+screened solves stream fewer columns. Also the paper's sparse simulation
+design (Section 7.1) as a statistical sanity check of a screened path with
+HBIC selection: the selected fit finds the true effects.
+"""
+import numpy as np
+import pytest
+
+from oracle import fsqrppa as O
+from oracle import select as S
+from paper_2601_02826_gb300 import synth
+from tests.gpu_helpers import to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2601_02826_gb300 import fsqr
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = fsqr.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+def _path(ctx, dw, w, taus, lams, **kw):
+    B = lams.size
+    beta = torch.zeros(B * w.P, dtype=torch.float64, device="cuda")
+    z = torch.zeros(B * w.n, dtype=torch.float64, device="cuda")
+    th = torch.zeros(B * w.n, dtype=torch.float64, device="cuda")
+    opts = dict(tol=1e-6, max_iter=900000, warm=2)
+    opts.update(kw)
+    rc, infos = ctx.fit_batch(dw.design, dw.y, taus, lams, dw.omega, w.block_ptr(), beta, z, th, opts=opts)
+    return rc, infos, to_np(beta).reshape(B, -1), to_np(z).reshape(B, -1), to_np(th).reshape(B, -1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_screened_path_meets_the_stop_test_on_the_full_design(ctx, precision):
+    from paper_2601_02826_gb300.device import upload
+    w = synth.tiny_geno(105, 300, 400, c=1, fmt=1, G=3, taus=(0.5,))
+    dw = upload(ctx, w)
+    d = O.build_design(O.decode_stored(w.geno, w.fmt, w.n), w.cov)
+    taus = [0.25, 0.5, 0.75]
+    fr = [0.6, 0.45, 0.3, 0.2, 0.15, 0.1]
+    lmaxs = [O.lambda_max(d.Xt, w.y, t, w.omega) for t in taus]
+    lams = np.array([[f * lm for f in fr] for lm in lmaxs])
+    ctx.profile(enable=False, reset=True)
+    rc, infos, bb, zz, tt = _path(ctx, dw, w, taus, lams, screen=1, precision=precision, max_group=3)
+    prof = ctx.profile()
+    assert rc == 0, [i.status for i in infos]
+    assert 0 < prof.screen_kept < prof.screen_total
+    rc0, _, bb0, _, _ = _path(ctx, dw, w, taus, lams, screen=0, precision=precision, max_group=3)
+    assert rc0 == 0
+    for t_i, tau in enumerate(taus):
+        for l_i in range(len(fr)):
+            f = t_i * len(fr) + l_i
+            lam = lams[t_i, l_i] * w.omega
+            ko = O.kkt(d.Xt, w.y, tau, lam, lmaxs[t_i], bb[f], zz[f], tt[f])
+            assert ko.value <= 1.001e-6, (f, ko)
+            assert O.objective(d.Xt, w.y, bb[f], tau, lam) == pytest.approx(
+                O.objective(d.Xt, w.y, bb0[f], tau, lam), rel=1e-6)
+
+
+def test_paper_sparse_design_screened_path_with_hbic(ctx):
+    """Section 7.1 design at (n, p) = (1000, 2000), tau = 0.5: the HBIC-selected
+    fit of a screened path selects the six fixed effects and X_p (the paper's
+    P1), and its coefficient error is in the range of Table 1's LASSO AE."""
+    from paper_2601_02826_gb300.device import upload
+    w = synth.paper_sparse(n=1000, p=2000, seed=7)
+    dw = upload(ctx, w)
+    d = O.build_design(O.decode_stored(w.geno, w.fmt, w.n), w.cov)
+    tau = 0.5
+    lmax = O.lambda_max(d.Xt, w.y, tau, w.omega)
+    fr = np.geomspace(0.5, 0.02, 10)
+    lams = np.array([[f * lmax for f in fr]])
+    rc, infos, bb, zz, tt = _path(ctx, dw, w, [tau], lams, screen=1, precision=0, max_group=1, tol=1e-5)
+    assert rc == 0, [i.status for i in infos]
+    B = len(fr)
+    _, act, hb = ctx.path_stats(dw.design, dw.y, [tau] * B, torch.from_numpy(bb.ravel()).cuda())
+    k = S.select(hb)
+    b_orig = O.back_transform(d, bb[k])
+    true = np.concatenate([[0.0], w.beta_true])
+    sel = set(np.flatnonzero(np.abs(b_orig[1:]) > 0) + 1)
+    assert {6, 20, 50, 100, 500, 1000, 2000} <= sel
+    assert np.sum(np.abs(b_orig[1:] - true[1:])) < 0.5
