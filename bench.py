@@ -514,11 +514,13 @@ def run_reference(args, rank, world):
 
 
 def run_grid_sample(args, local_rank):
-    """Batched-grid sample (not the contract line): the 10,000 x 500,000 int8
-    workload of the tau x lambda grid, one group of 8 fits (tau = 0.1..0.8
-    at 0.1 lambda_max) advanced together on the tensor cores for a fixed
-    number of iterations. Reports the time per iteration, the fit-iterations
-    per second and the column pass against the HBM roofline."""
+    """Batched-grid sample (not the contract line, and the small case for
+    profilers): the tau x lambda grid generator at n = 10,000 and p =
+    --grid-p columns (default 500,000), int8 or (--grid-2bit) 2-bit storage,
+    --grid-slots fits (taus 0.1..0.9, lambdas 0.3..0.03 lambda_max) advanced
+    together on the tensor cores for --profile-iters steps each (default
+    400). Reports the time per step, the fit-steps per second and the column
+    pass against the HBM roofline."""
     import torch
 
     from paper_2601_02826_gb300 import fsqr, synth
@@ -529,19 +531,27 @@ def run_grid_sample(args, local_rank):
     stream = torch.cuda.Stream(device=dev)
     ctx = fsqr.Context(local_rank, stream.cuda_stream)
     t0 = time.perf_counter()
-    w = synth.grid_int8()
+    slots = args.grid_slots
+    n_l = max(1, (slots + 8) // 9)
+    w = synth.grid_int8(p=args.grid_p, n_lambda=n_l)
+    if args.grid_2bit:
+        g = synth.unpack_int8(w.geno, w.n)
+        w.geno, w.ld = synth.pack_2bit(g)
+        w.fmt = synth.FMT_2BIT
     t_gen = time.perf_counter() - t0
     with torch.cuda.stream(stream):
         dw = upload(ctx, w, device=dev)
     stream.synchronize()
-    taus = w.taus[:8]
-    B = len(taus)
-    lam = [LAMBDA_FRAC * ctx.lambda_max(dw.design, dw.y, t, dw.omega) for t in taus]
+    taus = w.taus[:slots] if slots < 9 else w.taus
+    fr = np.geomspace(0.3, 0.03, n_l)
+    lm = [ctx.lambda_max(dw.design, dw.y, t, dw.omega) for t in taus]
+    lam = np.array([[f * l for f in fr] for l in lm])
+    B = lam.size
     beta = torch.zeros(B * w.P, dtype=torch.float64, device=dev)
     z = torch.zeros(B * w.n, dtype=torch.float64, device=dev)
     th = torch.zeros(B * w.n, dtype=torch.float64, device=dev)
     iters = args.profile_iters or 400
-    opts = dict(tol=0.0, max_iter=iters, precision=fsqr.MIXED, digits=4, max_group=8)
+    opts = dict(tol=0.0, max_iter=iters, precision=fsqr.MIXED, max_group=slots)
     ctx.fit_batch(dw.design, dw.y, taus, lam, dw.omega, w.block_ptr(), beta, z, th,
                   opts=dict(opts, max_iter=20))
     ctx.profile(enable=True, reset=True)
@@ -557,14 +567,15 @@ def run_grid_sample(args, local_rank):
     col_ms = prof.col_ms / max(1, prof.col_samples)
     peak, kind = measured_peaks()
     gbs = prof.col_bytes / (col_ms / 1e3) / 1e9
-    out = {"sample": "batched grid, one group of 8 fits, fixed iterations (setup included)",
-           "workload": "grid_int8", "n": w.n, "p": w.p, "G": len(w.block_sizes), "fits": B,
-           "iterations": iters, "ms": ms, "ms_per_iteration": ms / iters,
-           "fit_iterations_per_s": B * iters / (ms / 1e3),
+    out = {"sample": "batched grid, fixed steps per fit (setup included); not a bench line",
+           "workload": "grid_int8" + (" (2-bit storage)" if args.grid_2bit else ""), "n": w.n, "p": w.p,
+           "G": len(w.block_sizes), "fits": B, "slots": slots, "iterations": iters, "ms": ms,
+           "steps": prof.iterations, "fit_iterations_per_s": sum(i.iters for i in infos) / (ms / 1e3),
            "col": {"avg_launch_ms": col_ms, "bytes_per_launch": prof.col_bytes, "achieved_gbs": gbs,
                    "peak_gbs": peak, "frac": gbs / peak, "peak_source": kind},
            "xbeta_and_vector_update_ms": prof.xb_ms / max(1, prof.xb_samples),
-           "kkt_after": [i.kkt for i in infos], "generate_s": t_gen}
+           "groups": {"tc": prof.tc_groups, "wide": prof.wide_groups, "simt": prof.simt_groups},
+           "kkt_after": [i.kkt for i in infos][:4], "generate_s": t_gen}
     print(json.dumps(out))
 
 
@@ -587,6 +598,8 @@ def main():
     ap.add_argument("--grid-slots", type=int, default=32)
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: every fit stops after this many iterations (not a bench line)")
+    ap.add_argument("--grid-p", type=int, default=500_000)
+    ap.add_argument("--grid-2bit", action="store_true")
     ap.add_argument("--grid-sample", action="store_true",
                     help="batched-grid sample on the 10,000 x 500,000 workload (not a bench line)")
     args = ap.parse_args()

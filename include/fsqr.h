@@ -145,7 +145,7 @@ typedef struct {
                              R_b measures dist(s_j - gamma omega_j beta_j, lambda_j d|beta_j|),
                              info.primal includes the quadratic term and info.gap is NaN
                              when gamma > 0; default 0 (the weighted-l1 penalty) */
-  int32_t screen;         /* 1 (fsqr_fit_batch with FSQR_WARM_PATH, at most 8 taus): the
+  int32_t screen;         /* 1 (fsqr_fit_batch with FSQR_WARM_PATH, at most 32 taus): the
                              sequential strong rule along each tau's path. At stage l a stored
                              column j is left out of the stage's fits when, for every tau,
                              beta_j = 0 at lambda_{l-1} and |x~_j^T theta| < omega_j (2 lambda_l -

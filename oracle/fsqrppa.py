@@ -281,10 +281,16 @@ def kkt(Xt, y, tau, lam, lam_norm, beta, z, theta, s=None):
       R_1 = |1^T theta|
     lam_norm is lambda_max (1 when lambda_max is 0).
     """
-    n = len(y)
     if s is None:
         s = Xt.T @ theta
-    r_p = float(np.max(np.abs(y - Xt @ beta - z))) / (1.0 + float(np.max(np.abs(y))))
+    return kkt_from_products(y, tau, lam, lam_norm, beta, z, theta, Xt @ beta, s)
+
+
+def kkt_from_products(y, tau, lam, lam_norm, beta, z, theta, xb, s):
+    """The residuals of kkt() given the products xb = X~ beta and s = X~^T theta
+    (for designs formed one block of columns at a time)."""
+    n = len(y)
+    r_p = float(np.max(np.abs(y - xb - z))) / (1.0 + float(np.max(np.abs(y))))
     r_z = float(np.max(_dist_pinball_subgrad(n * theta, z, tau)))
     if len(beta) > 1:
         r_b = float(np.max(_dist_l1_subgrad(s[1:], lam[1:], beta[1:]))) / lam_norm

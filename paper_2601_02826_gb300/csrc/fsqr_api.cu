@@ -477,15 +477,16 @@ struct SolveEnv {
   double deadline_ms;        // <= 0: none
 };
 
-// The tensor-core passes run for int8 storage with at most 63 covariates and
-// sizes for which the integer arithmetic stays exact: a digit-product sum
-// over n samples (or over the active columns of an X~ beta split, at most
-// p) of |g t| <= 16 is a multiple of 2^-9 below 2^24 * 2^-9 in FP32 when
-// n, p <= 2^20; the recombined X~ beta, sum_j g_ij W_j with |W_j| < 2^43,
-// stays below 2^63 in int64 when p <= 2^19.
+// The tensor-core passes run for int8 or 2-bit storage with at most 63
+// covariates and sizes for which the integer arithmetic stays exact: a
+// digit-product sum over n samples of |g t| <= 16 is a multiple of 2^-9
+// below 2^24 * 2^-9 in FP32 when n <= 2^20. The X~ beta pass sums over the
+// active columns only; it checks at run time that fewer than 2^19 are active
+// (then its FP32 digit sums stay below 2^24 units and the recombined
+// sum_j g_ij W_j, |W_j| < 2^43, below 2^63) and reports an error otherwise.
 bool tc_eligible(const Dsg &X, int precision) {
-  return precision == FSQR_MIXED && X.fmt == FSQR_INT8 && X.p > 0 && X.c <= 63 && X.n <= ((int64_t)1 << 20) &&
-         X.p <= ((int64_t)1 << 19);
+  return precision == FSQR_MIXED && (X.fmt == FSQR_INT8 || X.fmt == FSQR_2BIT) && X.p > 0 && X.c <= 63 &&
+         X.n <= ((int64_t)1 << 20) && X.p <= ((int64_t)1 << 20);
 }
 
 int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
@@ -577,11 +578,16 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
     const int64_t nk = (n + 127) / 128;
     const int64_t ntile = (X.p + 127) / 128;
     TRY(wsget(ctx, "g_dgt", (size_t)(nk * N * 128), &dg));
-    TRY(wsget(ctx, "g_xt", (size_t)(ntile * nk * 16384), &xt));
     TRY(wsget(ctx, "g_err", 1, &d_err));
     CK(cudaMemsetAsync(dg, 0, (size_t)(nk * N * 128), st));
     CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-    LK(launch_tile_x(X, xt, nk, st));
+    if (X.fmt == FSQR_2BIT) {  // packed 4 KB tiles, expanded in the column pass
+      TRY(wsget(ctx, "g_xt2", (size_t)(ntile * nk * 4096), &xt));
+      LK(launch_tile_x2(X, xt, nk, st));
+    } else {
+      TRY(wsget(ctx, "g_xt", (size_t)(ntile * nk * 16384), &xt));
+      LK(launch_tile_x(X, xt, nk, st));
+    }
     const int64_t maxkb = (P + 127) / 128;
     TRY(wsget(ctx, "g_scol", (size_t)(maxkb * 128), &scol));
     TRY(wsget(ctx, "g_wtile", (size_t)(maxkb * xbeta_tc_rows(NB) * 128), &wtile));
@@ -591,7 +597,7 @@ int solve_group(fsqr_ctx *ctx, const SolveEnv &E, const GroupSpec &gs) {
               &tail_part));
     TRY(wsget(ctx, "g_tailtick", (size_t)std::max(1, tsc.rem), &tail_tick));
     CK(cudaMemsetAsync(tail_tick, 0, sizeof(unsigned) * (size_t)std::max(1, tsc.rem), st));
-    const size_t smem = col_tc_smem(NB, F.D, F.T);
+    const size_t smem = col_tc_smem(NB, F.D, F.T, X.fmt == FSQR_2BIT ? 1 : 0);
     if (smem > 200 * 1024)
       return fail(ctx, FSQR_EINVAL, "tensor-core column pass needs %zu B of shared memory", smem);
   }
@@ -1296,7 +1302,7 @@ int tune_group(fsqr_ctx *ctx, const SolveEnv &E, int B, int n_lambda, const doub
   std::vector<int> cand;
   for (int g : {1, 2, 3, 4, std::min(B, kMaxNB)})
     if (g <= B && (cand.empty() || g > cand.back())) cand.push_back(g);
-  if (tc_eligible(X, o->precision)) {  // wide slots (their fits run min(B, g) at a time)
+  if (tc_eligible(X, o->precision) && X.fmt == FSQR_INT8) {  // wide slots (their fits run min(B, g) at a time)
     if (B > kMaxNB) cand.push_back(16);
     if (B > 16) cand.push_back(kWideMax);
   }
@@ -1399,13 +1405,18 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
   for (int t = 0; t < n_tau * n_lambda; ++t)
     if (!(lambdas[t] >= 0.0) || isinf(lambdas[t]))
       return fail(ctx, FSQR_EINVAL, "lambda must be finite and >= 0");
-  if (opts->precision != FSQR_FP64 && Xd && Xd->geno_format != FSQR_INT8)
-    return fail(ctx, FSQR_EINVAL, "mixed precision needs FSQR_INT8 genotype storage");
+  if (opts->precision == FSQR_MIXED_SIMT && Xd && Xd->geno_format != FSQR_INT8)
+    return fail(ctx, FSQR_EINVAL, "FSQR_MIXED_SIMT needs FSQR_INT8 genotype storage");
+  if (opts->precision == FSQR_MIXED && Xd && Xd->geno_format == FSQR_DENSE_F64 && Xd->p > 0)
+    return fail(ctx, FSQR_EINVAL, "mixed precision needs genotype (int8 or 2-bit) storage");
   Prep pr;
   TRY(prepare(ctx, Xd, &pr, opts->precision != FSQR_FP64));
   const Dsg &X = pr.X;
   const int64_t P = X.P, n = X.n;
   TRY(check_blocks(ctx, block_ptr, G, P));
+  if (opts->precision == FSQR_MIXED && X.fmt == FSQR_2BIT && !tc_eligible(X, opts->precision))
+    return fail(ctx, FSQR_EINVAL,
+                "2-bit storage in FSQR_MIXED needs n, p <= 2^20 and at most 63 covariates; use FSQR_FP64");
   // omega: omega[0] == 0, omega >= 0; gap defined iff omega_j > 0 for j >= 1
   double om[2];
   {
@@ -1471,7 +1482,7 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
   const int B = n_tau * n_lambda;
   int mg = opts->max_group;
   if (mg == 0) TRY(tune_group(ctx, E, B, n_lambda, taus, lambdas, lmax, &mg));
-  if (mg > kMaxNB && tc_eligible(X, opts->precision)) {
+  if (mg > kMaxNB && tc_eligible(X, opts->precision) && X.fmt == FSQR_INT8) {
     // wide slots: every fit streams through 16 or 32 slots of one solve
     std::vector<WideFit> wf;
     for (int t = 0; t < n_tau; ++t)
@@ -1542,29 +1553,33 @@ int fit_batch_impl(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int n_
   return worst;
 }
 
-// s_out (host, nb x P) = X~^T theta_b for nb <= 8 fits whose theta sit at
-// th + b*n (device, fit-major): one full column pass.
-int full_xt(fsqr_ctx *ctx, const Prep &pr, const double *th, int nb, std::vector<double> &s_out) {
+// s_out (host, nf x P) = X~^T theta_b for nf fits whose theta sit at
+// th + b*n (device, fit-major): full column passes, 8 fits at a time.
+int full_xt(fsqr_ctx *ctx, const Prep &pr, const double *th, int nf, std::vector<double> &s_out) {
   const Dsg &X = pr.X;
   const int64_t n = X.n, npad = pad16(n), P = X.P;
   cudaStream_t st = ctx->stream;
-  const int NB = nb_template(nb);
   double *il, *sums, *s;
   TRY(wsget(ctx, "sc_thil", (size_t)npad * kMaxNB, &il));
   TRY(wsget(ctx, "sc_sums", kMaxNB, &sums));
   TRY(wsget(ctx, "sc_s", (size_t)P * kMaxNB, &s));
-  CK(cudaMemsetAsync(il, 0, sizeof(double) * npad * NB, st));
-  CK(cudaMemsetAsync(sums, 0, sizeof(double) * kMaxNB, st));
-  LK(launch_pack(th, n, il, n, nb, NB, npad, st));
-  LK(launch_sum_cols(th, n, n, nb, sums, nullptr, st));
+  s_out.assign((size_t)nf * P, 0.0);
+  std::vector<double> h((size_t)P * kMaxNB);
   Fits Fx = pass_fits(ctx, X);
-  LK(launch_col_pass(A_XT, NB, X, Fx, 0, il, sums, s, nullptr, st));
-  std::vector<double> h((size_t)P * NB);
-  CK(cudaMemcpyAsync(h.data(), s, sizeof(double) * P * NB, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  s_out.assign((size_t)nb * P, 0.0);
-  for (int b = 0; b < nb; ++b)
-    for (int64_t j = 0; j < P; ++j) s_out[(size_t)b * P + j] = h[(size_t)j * NB + b];
+  for (int b0 = 0; b0 < nf; b0 += kMaxNB) {
+    const int nb = std::min(kMaxNB, nf - b0);
+    const int NB = nb_template(nb);
+    const double *tb = th + (int64_t)b0 * n;
+    CK(cudaMemsetAsync(il, 0, sizeof(double) * npad * NB, st));
+    CK(cudaMemsetAsync(sums, 0, sizeof(double) * kMaxNB, st));
+    LK(launch_pack(tb, n, il, n, nb, NB, npad, st));
+    LK(launch_sum_cols(tb, n, n, nb, sums, nullptr, st));
+    LK(launch_col_pass(A_XT, NB, X, Fx, 0, il, sums, s, nullptr, st));
+    CK(cudaMemcpyAsync(h.data(), s, sizeof(double) * P * NB, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int b = 0; b < nb; ++b)
+      for (int64_t j = 0; j < P; ++j) s_out[(size_t)(b0 + b) * P + j] = h[(size_t)j * NB + b];
+  }
   return FSQR_OK;
 }
 
@@ -1585,7 +1600,7 @@ int fit_path_screened(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int
   TRY(check_opts(ctx, opts, G));
   if (n_tau < 1 || n_lambda < 1 || !taus || !lambdas) return fail(ctx, FSQR_EINVAL, "bad tau/lambda grid");
   if (!y || !omega || !beta || !z || !theta) return fail(ctx, FSQR_EINVAL, "NULL array argument");
-  if (n_tau > kMaxNB) return fail(ctx, FSQR_EINVAL, "screening takes at most %d quantiles", kMaxNB);
+  if (n_tau > kWideMax) return fail(ctx, FSQR_EINVAL, "screening takes at most %d quantiles", kWideMax);
   Prep pr;
   TRY(prepare(ctx, Xd, &pr, opts->precision != FSQR_FP64));
   const Dsg &X = pr.X;
@@ -1642,6 +1657,10 @@ int fit_path_screened(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int
       }
     }
     for (int round = 0;; ++round) {
+      // the reduced solve below re-prepares its own design in the same named
+      // workspace (statistics, affine maps, missing lists): prepare the full
+      // design again before its statistics and products are read
+      if (l > 0 || round > 0) TRY(prepare(ctx, Xd, &pr, opts->precision != FSQR_FP64));
       std::vector<int32_t> sel, idx;
       for (int64_t j = 0; j <= c; ++j) idx.push_back((int32_t)j);
       for (int64_t s = 0; s < p; ++s)
@@ -1693,6 +1712,10 @@ int fit_path_screened(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int
       Xr.col_mean = m_red;
       Xr.col_sd = s_red;
       fsqr_opts o2 = *opts;
+      if (opts->timeout_ms > 0) {  // one wall-clock budget for the whole path
+        const double left = (double)opts->timeout_ms - (now_ms() - t0);
+        o2.timeout_ms = (int64_t)std::max(1.0, left);
+      }
       o2.warm = FSQR_WARM_GIVEN;
       o2.screen = 0;
       o2.eta = etar.data();
@@ -1713,6 +1736,7 @@ int fit_path_screened(fsqr_ctx *ctx, const fsqr_design *Xd, const double *y, int
                            cudaMemcpyDeviceToDevice, st));
       }
       // the stop test's R_b over the left-out columns, on the full design
+      TRY(prepare(ctx, Xd, &pr, opts->precision != FSQR_FP64));
       std::vector<double> sfull;
       TRY(full_xt(ctx, pr, t_st, n_tau, sfull));
       bool viol = false;

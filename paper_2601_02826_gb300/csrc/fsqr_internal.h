@@ -147,6 +147,7 @@ cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, c
                           const uint8_t *dgt, const TcSchedule &sc, int32_t *tail_part,
                           unsigned *tail_tick, int *err, cudaStream_t s);
 cudaError_t launch_tile_x(const Dsg &X, uint8_t *xt, int64_t nk, cudaStream_t s);
+cudaError_t launch_tile_x2(const Dsg &X, uint8_t *xt, int64_t nk, cudaStream_t s);  // 2-bit, 4 KB tiles
 
 // Wide groups (k_wide.cu), NB in {16, 32} slots. Digit matrix: 8 NB rows x
 // npad E4M3 bytes (tiled as for k_quantize_tc); X~ beta weight tiles:
@@ -175,7 +176,7 @@ cudaError_t launch_xbeta_tc(int NB, const Dsg &X, const Fits &F, int off, int fu
                             int *scol, uint8_t *wtile, int *err, int num_sms, cudaStream_t s);
 int xbeta_tc_rows(int NB);
 cudaError_t launch_quantize_tc(int NB, int D, const Fits &F, int off, uint8_t *dg, cudaStream_t s);
-size_t col_tc_smem(int NB, int D, int T);
+size_t col_tc_smem(int NB, int D, int T, int f2);
 int tc_rows(int NB, int D);
 
 // Learned warm start (k_mlp.cu): a 3 -> 256 -> 256 -> 256 -> 1 ReLU network

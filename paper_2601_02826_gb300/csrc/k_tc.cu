@@ -48,7 +48,7 @@ using namespace sm103;
 __constant__ uint8_t kE4M3Int[17] = {0xD0, 0xCE, 0xCC, 0xCA, 0xC8, 0xC4, 0xC0, 0xB8, 0x00,
                                      0x38, 0x40, 0x44, 0x48, 0x4A, 0x4C, 0x4E, 0x50};
 
-template <int NB, int D>
+template <int NB, int D, int F2 = 0>
 struct TcShape {
   static constexpr int NR = NB * D;
   static constexpr int N = NR <= 16 ? 16 : (NR <= 32 ? 32 : 64);
@@ -57,9 +57,39 @@ struct TcShape {
   static constexpr int STAGES = 6;
   static constexpr int A_BYTES = 128 * 128;
   static constexpr int B_BYTES = N * 128;
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int THREADS = 256;
+  // 2-bit storage (F2): the stage also holds the 4 KB packed tile that the
+  // decode warps expand into the A operand
+  static constexpr int RAW_BYTES = F2 ? 128 * 32 : 0;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES + RAW_BYTES;
+  static constexpr int THREADS = F2 ? 384 : 256;
 };
+
+// Four 2-bit genotype codes (one byte, sample 4q + f in bits 2f) -> four
+// bytes holding the codes 0/1/2, which read as E4M3 are exactly g * 2^-9;
+// the missing code 3 becomes 0 (mean imputation is applied by the
+// correction terms).
+__device__ __forceinline__ uint32_t spread_codes(uint32_t b) {
+  uint32_t v = (b & 3u) | ((b & 0xCu) << 6) | ((b & 0x30u) << 12) | ((b & 0xC0u) << 18);
+  const uint32_t m = v & (v >> 1) & 0x01010101u;
+  return v & ~(m * 3u);
+}
+
+// As spread_codes for codes already in 0..2 (the sanitised 2-bit tiles): byte
+// k of w (codes 4k .. 4k+3) goes to one output word in two shift-and-mask steps.
+__device__ __forceinline__ uint32_t spread_clean(uint32_t w, int k) {
+  uint32_t x = __byte_perm(w, 0u, 0x4440u | (uint32_t)k);  // byte k, zero-extended
+  x = (x | (x << 12)) & 0x000F000Fu;
+  return (x | (x << 6)) & 0x03030303u;
+}
+
+__device__ __forceinline__ uint4 spread_word_clean(uint32_t w) {
+  return make_uint4(spread_clean(w, 0), spread_clean(w, 1), spread_clean(w, 2), spread_clean(w, 3));
+}
+
+__device__ __forceinline__ uint4 spread_word(uint32_t w) {
+  return make_uint4(spread_codes(w & 0xffu), spread_codes((w >> 8) & 0xffu), spread_codes((w >> 16) & 0xffu),
+                    spread_codes(w >> 24));
+}
 
 // At most this many sample slices per tail tile.
 constexpr int kMaxTailSlices = 16;
@@ -114,17 +144,22 @@ __device__ __forceinline__ bool col_update(const Dsg &X, const Fits &F, int64_t 
   return act;
 }
 
-template <int NB, int D>
-__global__ void __launch_bounds__(256, 1)
+// F2 = 1: 2-bit storage. xt then holds tiles of 128 columns x 128 samples
+// of packed codes (32 bytes per column, 4 KB per tile, missing codes already
+// 0), the producer bulk-copies them into the stage's raw area, and warps
+// 8-11 (one thread per tile row) expand them into the E4M3 A operand before
+// releasing the stage to the MMA issuer.
+template <int NB, int D, int F2>
+__global__ void __launch_bounds__(F2 ? 384 : 256, 1)
     k_col_tc(Dsg X, Fits F, int off, const uint8_t *__restrict__ xt, const uint8_t *__restrict__ dgt,
              int rounds, int slices, int32_t *__restrict__ tail_part, unsigned *__restrict__ tail_tick,
              int *err) {
-  using Sh = TcShape<NB, D>;
+  using Sh = TcShape<NB, D, F2>;
   constexpr int N = Sh::N;
   constexpr int S = Sh::STAGES;
   constexpr int kAcc = Sh::ACC;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[S], empty[S], accf[kAcc], acce[kAcc], drain;
+  __shared__ __align__(8) uint64_t full[S], empty[S], dec[S], accf[kAcc], acce[kAcc], drain;
   __shared__ uint32_t tmem_base;
   __shared__ double sS[kMaxNB], sScale[kMaxNB];
   __shared__ int sIdle[kMaxNB];
@@ -156,7 +191,7 @@ __global__ void __launch_bounds__(256, 1)
   const int tail_k0 = ns ? nk * tv / ns : 0, tail_k1 = ns ? nk * (tv + 1) / ns : 0;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); mbar_init(&dec[s], 128); }
     for (int a = 0; a < kAcc; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], 128); }
     mbar_init(&drain, 1);
     fence_mbar_init();
@@ -191,8 +226,14 @@ __global__ void __launch_bounds__(256, 1)
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, err, kErrEmpty)) goto producer_done;
           uint8_t *sa = ring + s * Sh::STAGE_BYTES;
-          mbar_arrive_expect_tx(&full[s], Sh::STAGE_BYTES);
-          bulk_load(sa, xt + ((int64_t)tile * nk + kc) * Sh::A_BYTES, Sh::A_BYTES, &full[s]);
+          if (F2) {
+            mbar_arrive_expect_tx(&full[s], Sh::RAW_BYTES + Sh::B_BYTES);
+            bulk_load(sa + Sh::A_BYTES + Sh::B_BYTES, xt + ((int64_t)tile * nk + kc) * Sh::RAW_BYTES,
+                      Sh::RAW_BYTES, &full[s]);
+          } else {
+            mbar_arrive_expect_tx(&full[s], Sh::A_BYTES + Sh::B_BYTES);
+            bulk_load(sa, xt + ((int64_t)tile * nk + kc) * Sh::A_BYTES, Sh::A_BYTES, &full[s]);
+          }
           bulk_load(sa + Sh::A_BYTES, dgt + (int64_t)kc * Sh::B_BYTES, Sh::B_BYTES, &full[s]);
         }
       }
@@ -214,7 +255,8 @@ __global__ void __launch_bounds__(256, 1)
         for (int kc = k0; kc < k1; ++kc, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
-          if (!mbar_wait(&full[s], ph, err, kErrFull)) { ok = false; break; }
+          // F2: the decode warps' arrival implies the bulk copies landed
+          if (!mbar_wait(F2 ? &dec[s] : &full[s], ph, err, kErrFull)) { ok = false; break; }
           tc_fence_after();
           const uint32_t sa = smem_u32(ring + s * Sh::STAGE_BYTES);
           const uint64_t ad = sdesc_k128(sa), bd = sdesc_k128(sa + Sh::A_BYTES);
@@ -229,6 +271,31 @@ __global__ void __launch_bounds__(256, 1)
       // wait for every MMA issued so far before the TMEM is released
       mma_commit(&drain);
       mbar_wait(&drain, 0u, err, kErrFull);
+    }
+  } else if (warp >= 8) {
+    // ------------------------------------------- 2-bit decode (F2 only)
+    // thread m expands row m (tile column m): its 32 packed bytes (128
+    // samples) become 8 swizzled 16-byte chunks of the K-major operand
+    const int m = threadIdx.x - 256;
+    int it = 0;
+    for (int lt = 0; lt < ntl; ++lt) {
+      const int k0 = lt < R ? 0 : tail_k0, k1 = lt < R ? nk : tail_k1;
+      bool ok = true;
+      for (int kc = k0; kc < k1; ++kc, ++it) {
+        const int s = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
+        if (!mbar_wait(&full[s], ph, err, kErrFull)) { ok = false; break; }
+        uint8_t *sa = ring + s * Sh::STAGE_BYTES;
+        const uint4 *raw = reinterpret_cast<const uint4 *>(sa + Sh::A_BYTES + Sh::B_BYTES + m * 32);
+        const uint4 r0 = raw[0], r1 = raw[1];
+        const uint32_t wv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          *reinterpret_cast<uint4 *>(sa + m * 128 + ((c ^ (m & 7)) << 4)) = spread_word_clean(wv[c]);
+        fence_proxy_async();
+        mbar_arrive(&dec[s]);
+      }
+      if (!ok) break;
     }
   } else if (warp >= 6) {
     // --------------------------------------------------- dense columns (FP64)
@@ -345,9 +412,11 @@ __global__ void __launch_bounds__(256, 1)
   }
   // per-CTA reductions in a fixed order
   for (int b = 0; b < NB; ++b) {
-    red[0][threadIdx.x] = rbl[b];
-    red[1][threadIdx.x] = ctl[b];
-    red[2][threadIdx.x] = wml[b];
+    if (threadIdx.x < 256) {  // the decode warps (F2) hold no partials
+      red[0][threadIdx.x] = rbl[b];
+      red[1][threadIdx.x] = ctl[b];
+      red[2][threadIdx.x] = wml[b];
+    }
     __syncthreads();
     const int ops[3] = {0, 1, 0};
     tree_reduce<3>(red, ops, 256);
@@ -437,9 +506,11 @@ __global__ void __launch_bounds__(256, 1)
                                 ie);
       }
       for (int b = 0; b < NB; ++b) {
-        red[0][threadIdx.x] = rb2[b];
-        red[1][threadIdx.x] = ct2[b];
-        red[2][threadIdx.x] = wm2[b];
+        if (threadIdx.x < 256) {
+          red[0][threadIdx.x] = rb2[b];
+          red[1][threadIdx.x] = ct2[b];
+          red[2][threadIdx.x] = wm2[b];
+        }
         __syncthreads();
         const int ops[3] = {0, 1, 0};
         tree_reduce<3>(red, ops, 256);
@@ -578,10 +649,15 @@ struct XbShape {
 
 constexpr int kXTMaxSplits = 16;
 
+// The recombined integer sum_j g_ij W_j (|W_j| < 2^43, g <= 2) stays below
+// 2^63 and every FP32 digit sum below 2^24 units while fewer than 2^19
+// columns are active; beyond that the pass records an error and adds nothing.
+constexpr int kMaxActive = 1 << 19;
+
 template <int NB, int DWD>
 __global__ void __launch_bounds__(128)
     k_xprep(Dsg X, Fits F, int off, const double *__restrict__ beta_in, int split_cap, int *__restrict__ scol,
-            uint8_t *__restrict__ wtile) {
+            uint8_t *__restrict__ wtile, int *err) {
   using Sh = XbShape<NB, DWD>;
   extern __shared__ int spre[];  // gridA + 1
   __shared__ double sInv[kMaxNB];
@@ -591,7 +667,11 @@ __global__ void __launch_bounds__(128)
     beta = F.beta[(k & 1) ^ 1];
   }
   const int gA = F.gridA;
-  const int A = __ldcg(F.a_pre + gA);
+  int A = __ldcg(F.a_pre + gA);
+  if (A >= kMaxActive) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(err, 0, 5);
+    A = 0;
+  }
   const int nkb = (A + 127) / 128;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     // splits of the X~ beta pass: enough CTAs for one resident wave
@@ -721,14 +801,32 @@ __global__ void __launch_bounds__(128)
         const int s = it % ST;
         if (!mbar_wait(&empty[s], ((uint32_t)(it / ST) & 1u) ^ 1u, err, kErrEmpty)) { ok = false; return; }
         uint8_t *stage = ring + s * Sh::BUF;
+        if (X.fmt == FSQR_2BIT) {
+          // 16 packed samples = 4 bytes per column (in bounds: s0/4 + 4 <= ld):
+          // all 8 loads first, then the codes past n cleared and expanded to
+          // E4M3 bytes in registers
+          uint32_t wv[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int kk = 16 * e + kr;
-          uint8_t *dst = stage + kk * 128 + ((c ^ (kk & 7)) << 4);
-          if (valid > 0 && idx[e] < X.p)
-            cp_async16(dst, X.geno + (int64_t)idx[e] * X.ld + s0, valid);  // bytes past n zero-filled
-          else
-            *reinterpret_cast<int4 *>(dst) = make_int4(0, 0, 0, 0);
+          for (int e = 0; e < 8; ++e)
+            wv[e] = (valid > 0 && idx[e] < X.p)
+                        ? __ldg(reinterpret_cast<const uint32_t *>(X.geno + (int64_t)idx[e] * X.ld + (s0 >> 2)))
+                        : 0u;
+          const uint32_t keep = valid >= 16 ? 0xffffffffu : ((1u << (2 * valid)) - 1u);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int kk = 16 * e + kr;
+            *reinterpret_cast<uint4 *>(stage + kk * 128 + ((c ^ (kk & 7)) << 4)) = spread_word(wv[e] & keep);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int kk = 16 * e + kr;
+            uint8_t *dst = stage + kk * 128 + ((c ^ (kk & 7)) << 4);
+            if (valid > 0 && idx[e] < X.p)
+              cp_async16(dst, X.geno + (int64_t)idx[e] * X.ld + s0, valid);  // bytes past n zero-filled
+            else
+              *reinterpret_cast<int4 *>(dst) = make_int4(0, 0, 0, 0);
+          }
         }
         if (tid == 0) {
           // the digit tile adds transaction bytes to the phase; the 128
@@ -924,7 +1022,7 @@ static cudaError_t xbeta_tc_t(const Dsg &X, const Fits &F, int off, int fuse, co
   const int maxkb = (int)((X.P + 127) / 128);
   const int pgrid = std::max(1, std::min(maxkb, num_sms));
   const size_t psmem = (size_t)(F.gridA + 1) * sizeof(int);
-  k_xprep<NB, DWD><<<pgrid, 128, psmem, s>>>(X, F, off, beta_in, split_cap, scol, wtile);
+  k_xprep<NB, DWD><<<pgrid, 128, psmem, s>>>(X, F, off, beta_in, split_cap, scol, wtile, err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)rows, kXTMaxSplits);
@@ -949,12 +1047,12 @@ int xbeta_tc_rows(int NB) { return ((NB * 11 + 15) / 16) * 16; }
 
 // ------------------------------------------------------------------ host
 
-template <int NB, int D>
+template <int NB, int D, int F2>
 size_t g_tc_opted = 0;  // the attribute is set on first use
 
-size_t col_tc_smem(int NB, int D, int T) {
+size_t col_tc_smem(int NB, int D, int T, int f2) {
   int N = NB * D <= 16 ? 16 : (NB * D <= 32 ? 32 : 64);
-  return (size_t)6 * (128 * 128 + N * 128) + 1024 + (size_t)T + 16;  // flags use <= T bytes
+  return (size_t)6 * (128 * 128 + N * 128 + (f2 ? 4096 : 0)) + 1024 + (size_t)T + 16;  // flags use <= T bytes
 }
 
 void col_tc_schedule(int64_t p, int64_t n, int num_sms, TcSchedule *out) {
@@ -975,26 +1073,30 @@ void col_tc_schedule(int64_t p, int64_t n, int num_sms, TcSchedule *out) {
 
 int tc_tail_rows(int NB, int D) { return NB * D; }
 
-template <int NB, int D>
+template <int NB, int D, int F2>
 static cudaError_t col_tc_t(const Dsg &X, const Fits &F, int off, const uint8_t *xt,
                             const uint8_t *dgt, const TcSchedule &sc, int32_t *tail_part,
                             unsigned *tail_tick, int *err, cudaStream_t s) {
-  const size_t smem = col_tc_smem(NB, D, F.T);
-  if (smem > g_tc_opted<NB, D>) {
-    cudaError_t e = cudaFuncSetAttribute(k_col_tc<NB, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = col_tc_smem(NB, D, F.T, F2);
+  if (smem > g_tc_opted<NB, D, F2>) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_col_tc<NB, D, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    g_tc_opted<NB, D> = smem;
+    g_tc_opted<NB, D, F2> = smem;
   }
-  k_col_tc<NB, D><<<sc.grid, TcShape<NB, D>::THREADS, smem, s>>>(X, F, off, xt, dgt, sc.rounds, sc.slices,
-                                                                   tail_part, tail_tick, err);
+  k_col_tc<NB, D, F2><<<sc.grid, TcShape<NB, D, F2>::THREADS, smem, s>>>(X, F, off, xt, dgt, sc.rounds, sc.slices,
+                                                                           tail_part, tail_tick, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_col_tc(int NB, int D, const Dsg &X, const Fits &F, int off, const uint8_t *xt,
                           const uint8_t *dgt, const TcSchedule &sc, int32_t *tail_part,
                           unsigned *tail_tick, int *err, cudaStream_t s) {
-#define FSQR_TC_CASE(nb, d) \
-  if (NB == nb && D == d) return col_tc_t<nb, d>(X, F, off, xt, dgt, sc, tail_part, tail_tick, err, s);
+  const bool f2 = X.fmt == FSQR_2BIT;
+#define FSQR_TC_CASE(nb, d)                                                                   \
+  if (NB == nb && D == d)                                                                     \
+    return f2 ? col_tc_t<nb, d, 1>(X, F, off, xt, dgt, sc, tail_part, tail_tick, err, s)      \
+              : col_tc_t<nb, d, 0>(X, F, off, xt, dgt, sc, tail_part, tail_tick, err, s);
   FSQR_TC_CASE(1, 7) FSQR_TC_CASE(2, 7) FSQR_TC_CASE(3, 7) FSQR_TC_CASE(4, 7) FSQR_TC_CASE(8, 7)
   FSQR_TC_CASE(1, 6) FSQR_TC_CASE(2, 6) FSQR_TC_CASE(3, 6) FSQR_TC_CASE(4, 6) FSQR_TC_CASE(8, 6)
 #undef FSQR_TC_CASE
@@ -1013,6 +1115,43 @@ cudaError_t launch_quantize_tc(int NB, int D, const Fits &F, int off, uint8_t *d
 }
 
 int tc_rows(int NB, int D) { return NB * D <= 16 ? 16 : (NB * D <= 32 ? 32 : 64); }
+
+// 2-bit storage: tile (t, kc) at xt + (t*nk + kc)*4096, row m = column
+// 128t + m, 32 bytes = its samples 128kc .. 128kc+127 packed 4 per byte as
+// stored, with missing codes (3) and samples >= n or columns >= p set to 0.
+__global__ void k_tile_x2(Dsg X, uint8_t *xt, int64_t nk) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte half row
+  const int64_t ntile = (X.p + 127) / 128;
+  if (g >= ntile * nk * 256) return;
+  const int64_t tk = g >> 8;
+  const int q = (int)(g & 255), m = q >> 1, h = q & 1;
+  const int64_t t = tk / nk, kc = tk - t * nk;
+  const int64_t col = t * 128 + m;
+  const int64_t b0 = kc * 32 + 16 * h;  // first source byte
+  uint8_t out[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    uint32_t byte = 0;
+    if (col < X.p && b0 + u < X.ld) byte = X.geno[col * X.ld + b0 + u];
+    uint32_t o = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int64_t i = 4 * (b0 + u) + f;
+      uint32_t code = (byte >> (2 * f)) & 3u;
+      if (code == 3u || i >= X.n) code = 0u;
+      o |= code << (2 * f);
+    }
+    out[u] = (uint8_t)o;
+  }
+  *reinterpret_cast<uint4 *>(xt + tk * 4096 + (int64_t)q * 16) = *reinterpret_cast<const uint4 *>(out);
+}
+
+cudaError_t launch_tile_x2(const Dsg &X, uint8_t *xt, int64_t nk, cudaStream_t s) {
+  const int64_t halves = (X.p + 127) / 128 * nk * 256;
+  if (halves == 0) return cudaSuccess;
+  k_tile_x2<<<(unsigned)((halves + 255) / 256), 256, 0, s>>>(X, xt, nk);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tile_x(const Dsg &X, uint8_t *xt, int64_t nk, cudaStream_t s) {
   const int64_t chunks = (X.p + 127) / 128 * nk * 1024;

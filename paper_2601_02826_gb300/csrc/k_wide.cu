@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(256) k_slot_init(Fits F, int par, const int *_
 template <int NB>
 __global__ void __launch_bounds__(128)
     k_wxprep(Dsg X, Fits F, int off, const double *__restrict__ beta_in, int split_cap, int *__restrict__ scol,
-             uint8_t *__restrict__ wtile) {
+             uint8_t *__restrict__ wtile, int *err) {
   using Sh = WXShape<NB>;
   extern __shared__ int spre[];  // gridA + 1
   __shared__ double sInv[NB];
@@ -516,7 +516,11 @@ __global__ void __launch_bounds__(128)
     beta = F.beta[(k & 1) ^ 1];
   }
   const int gA = F.gridA;
-  const int A = __ldcg(F.a_pre + gA);
+  int A = __ldcg(F.a_pre + gA);
+  if (A >= (1 << 19)) {  // the exact integer sums need fewer than 2^19 active columns
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(err, 0, 5);
+    A = 0;
+  }
   const int nkb = (A + 127) / 128;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     F.meta_i[0] = max(1, min(16, min(nkb, split_cap)));
@@ -886,7 +890,7 @@ static cudaError_t wxbeta_t(const Dsg &X, const Fits &F, int off, int fuse, cons
   const int maxkb = (int)((X.P + 127) / 128);
   const int pgrid = std::max(1, std::min(maxkb, num_sms));
   const size_t psmem = (size_t)(F.gridA + 1) * sizeof(int);
-  k_wxprep<NB><<<pgrid, 128, psmem, s>>>(X, F, off, beta_in, split_cap, scol, wtile);
+  k_wxprep<NB><<<pgrid, 128, psmem, s>>>(X, F, off, beta_in, split_cap, scol, wtile, err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)rows, 16);
