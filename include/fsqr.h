@@ -75,10 +75,12 @@ extern "C" {
                              codes read as E4M3, FP32 accumulation that stays
                              exact; X~ beta likewise from base-16 digits of
                              a_j beta_j over the active columns, int64 sums.
-                             int8 storage only; tensor cores with <= 63
-                             covariates, n <= 2^20 and p <= 2^19 (where
-                             the digit sums stay exact), else the kernels of
-                             FSQR_MIXED_SIMT. */
+                             int8 or 2-bit storage; tensor cores with <= 63
+                             covariates and n, p <= 2^20 (where the digit sums
+                             stay exact; the X~ beta pass also needs fewer than
+                             2^19 active columns and fails with FSQR_ECUDA
+                             beyond), else for int8 the kernels of
+                             FSQR_MIXED_SIMT and for 2-bit FSQR_EINVAL. */
 #define FSQR_MIXED_SIMT 2 /* as FSQR_MIXED, with X~^T theta from int8 digits of
                              theta by DP4A on the SIMT cores instead */
 

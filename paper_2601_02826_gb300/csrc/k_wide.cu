@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(256, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = *F.it_base + off;
+  const bool chk = (k % F.K) == 0;  // a stop-test step
   const double *bcur = F.beta[k & 1];
   double *bnxt = F.beta[(k & 1) ^ 1];
   const int64_t ntiles = (X.p + 127) / 128;
@@ -341,6 +342,7 @@ __global__ void __launch_bounds__(256, 1)
             const float e32 = (fabsf(t1) + fabsf(t2)) * 4.76837158203125e-7f;
             zero = fabsf(s32) + e32 < sLamf[b] * omf;
           }
+          float wmf = 0.0f;
           if (zero) {
             bn2[h] = 0.0;
           } else if (live && !sIdle[b]) {
@@ -348,19 +350,25 @@ __global__ void __launch_bounds__(256, 1)
             const double mc = X.mptr ? miss_dot(X, sidx, F.theta, NB, b) : 0.0;
             const double s = aj * ((double)V * sScale[b]) + bj * (sS[b] - mc);
             const double lamj = sLam[b] * om;
-            rb = wdist(gj == 0.0 ? s : s - gj * bo, lamj, bo);
+            // the stop test reads the distance only at its own steps
+            if (chk) rb = wdist(gj == 0.0 ? s : s - gj * bo, lamj, bo);
+            // eq. beta_update: the soft threshold of av at lamj, over eta_g (+ gamma_j)
             const double av = eta * bo + s;
-            const double bn = (fmax(av - lamj, 0.0) - fmax(-av - lamj, 0.0)) * ie;
+            const double bn = fabs(av) > lamj ? copysign(fabs(av) - lamj, av) * ie : 0.0;
             bn2[h] = bn;
             ct = bj * bn;
             act = act || (bn != 0.0);
-            wm = fabs(aj * bn);
+            // max |a_j beta_j| only sets the power-of-two scale of the X~ beta
+            // digits: rounded up to FP32 it stays an upper bound
+            wmf = __double2float_ru(fabs(aj * bn));
           }
           // the warp's partials (skipped when every lane's are zero)
-          if (__any_sync(0xffffffffu, rb != 0.0 || ct != 0.0 || wm != 0.0)) {
-            rb = wmax32(rb);
+          if (__any_sync(0xffffffffu, rb != 0.0 || ct != 0.0 || wmf != 0.0f)) {
+            if (chk) rb = wmax32(rb);
             ct = wsum32(ct);
-            wm = wmax32(wm);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) wmf = fmaxf(wmf, __shfl_xor_sync(0xffffffffu, wmf, o));
+            wm = (double)wmf;
             if (lane == 0) {
               s_part[q][b][0] = fmax(s_part[q][b][0], rb);
               s_part[q][b][1] += ct;
