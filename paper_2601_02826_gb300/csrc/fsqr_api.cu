@@ -340,8 +340,17 @@ int lambda_max_dev(fsqr_ctx *ctx, const Prep &pr, const double *y, double tau, c
   LK(launch_select(y, n, k, q, ctx->stream));
   LK(launch_lmax_vec(y, n, npad, tau, q, v, ctx->stream));
   LK(launch_sum_cols(v, n, npad, 1, vs, nullptr, ctx->stream));
-  Fits F = pass_fits(ctx, X);
-  LK(launch_col_pass(A_XT, 1, X, F, 0, v, vs, s, nullptr, ctx->stream));
+  if (X.fmt == FSQR_DENSE_F64) {
+    Fits F = pass_fits(ctx, X);
+    LK(launch_col_pass(A_XT, 1, X, F, 0, v, vs, s, nullptr, ctx->stream));
+  } else {  // int8 / 2-bit codes: exact integer products with v in 52-bit fixed point
+    int2 *vq;
+    double *vu;
+    TRY(wsget(ctx, "lmax_vq", npad, &vq));
+    TRY(wsget(ctx, "lmax_vu", 1, &vu));
+    LK(launch_fix_seg(v, nullptr, nullptr, nullptr, npad, 1, 0, vq, vu, nullptr, ctx->stream));
+    LK(launch_xtv_int(X, nullptr, 1, v, vq, vu, vs, npad, s, ctx->stream));
+  }
   LK(launch_colmax_ratio(s, omega, X.P, (double)n, o, ctx->stream));
   *out = LmaxDev{q, s, o};
   return FSQR_OK;
@@ -395,14 +404,36 @@ int eta_impl(fsqr_ctx *ctx, const Prep &pr, const int64_t *bp, int G, double mu,
   Fits F = pass_fits(ctx, X);
   F.block_ptr = d_bp;
   F.G = G;
+  // int8 / 2-bit codes: both products exact in integers, the vectors in
+  // 52-bit fixed point (v per split with its a_j, u per block)
+  const bool exact = X.fmt != FSQR_DENSE_F64;
+  int2 *qv = nullptr, *qu = nullptr;
+  double *uv = nullptr, *cv = nullptr, *uu = nullptr;
+  if (exact) {
+    TRY(wsget(ctx, "pw_qv", P, &qv));
+    TRY(wsget(ctx, "pw_uv", nsplit, &uv));
+    TRY(wsget(ctx, "pw_cv", nsplit, &cv));
+    TRY(wsget(ctx, "pw_qu", (size_t)G * npad, &qu));
+    TRY(wsget(ctx, "pw_uu", G, &uu));
+  }
   std::vector<double> lam(G, 0.0), res(G, 0.0), hq(G), hw(G);
   std::vector<char> frozen(G, 0);
   int left = G;
   for (int t = 1; t <= max_iter && left > 0; ++t) {
-    LK(launch_xv_blocks(X, v, d_splits, d_sob, G, nsplit, U, npad, part, ctx->stream));
+    if (exact) {
+      LK(launch_fix_seg(v, X.a, X.b, d_splits, 0, nsplit, 1 + X.c, qv, uv, cv, ctx->stream));
+      LK(launch_xv_blocks_int(X, v, d_splits, d_sob, G, nsplit, qv, uv, cv, U, npad, part, ctx->stream));
+    } else {
+      LK(launch_xv_blocks(X, v, d_splits, d_sob, G, nsplit, U, npad, part, ctx->stream));
+    }
     if (X.mptr) LK(launch_miss_xv(X, v, d_bp, G, U, npad, ctx->stream));
     LK(launch_sum_cols(U, n, npad, G, usum, usq, ctx->stream));
-    LK(launch_col_pass(A_XT_BLOCK, 1, X, F, 0, U, usum, w, nullptr, ctx->stream));
+    if (exact) {
+      LK(launch_fix_seg(U, nullptr, nullptr, nullptr, npad, G, 0, qu, uu, nullptr, ctx->stream));
+      LK(launch_xtv_int(X, d_bp, G, U, qu, uu, usum, npad, w, ctx->stream));
+    } else {
+      LK(launch_col_pass(A_XT_BLOCK, 1, X, F, 0, U, usum, w, nullptr, ctx->stream));
+    }
     LK(launch_power_step(w, d_bp, G, P, v, wn, ctx->stream));
     CK(cudaMemcpyAsync(hq.data(), usq, G * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(hw.data(), wn, G * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

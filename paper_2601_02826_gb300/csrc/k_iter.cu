@@ -492,6 +492,107 @@ cudaError_t launch_col_pass(int mode, int NB, const Dsg &X, const Fits &F, int o
   }
 }
 
+// ------------------------------------ X~^T u with exact integer products
+//
+// s_out[j] = x~_j^T u_g(j) for one vector per block (the power method's
+// X~_g^T u_g; lambda_max with G = 1). u_g is given both in FP64 (u) and as
+// 52-bit fixed point q_i = hi_i 2^26 + lo_i with unit[g] (k_fix_seg over the
+// blocks' npad-long segments, so entries i >= n are 0). For stored int8 and
+// 2-bit columns, sum_i x_ij q_i is exact in two int64 sums (codes 0/1/2, a
+// missing code read as 0 and its share b_j u_i taken back out); one warp takes
+// 4 consecutive columns of one block. The intercept, the covariates and the
+// groups that straddle a block boundary or the end take the FP64 dot.
+__global__ void __launch_bounds__(256) k_xtv_int(Dsg X, const int64_t *__restrict__ bp, int G,
+                                                 const double *__restrict__ u, const int2 *__restrict__ q,
+                                                 const double *__restrict__ unit, const double *__restrict__ usum,
+                                                 int64_t npad, double *__restrict__ s_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t ngrp = (X.P + 3) >> 2;
+  const int64_t nch = (X.n + 15) >> 4;  // 16-sample chunks; 16 nch <= npad
+  for (int64_t gi = (int64_t)blockIdx.x * kAWarps + (threadIdx.x >> 5); gi < ngrp;
+       gi += (int64_t)gridDim.x * kAWarps) {
+    const int64_t j0 = gi * 4, j1 = min(X.P, j0 + 4);
+    const int g0 = block_of(bp, G, j0);
+    const bool fast = j0 > X.c && j1 - j0 == 4 && block_of(bp, G, j1 - 1) == g0 && X.fmt != FSQR_DENSE_F64;
+    double d[4] = {0.0, 0.0, 0.0, 0.0};
+    if (fast) {
+      long long ahi[4] = {0, 0, 0, 0}, alo[4] = {0, 0, 0, 0};
+      const int4 *qg = reinterpret_cast<const int4 *>(q + (int64_t)g0 * npad);
+      const uint8_t *cp[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cp[k] = col_ptr(X, j0 + k);
+      for (int64_t ch = lane; ch < nch; ch += 32) {
+        // codes of samples 16ch .. 16ch+15 as four 32-bit words per column
+        uint32_t cw[4][4];
+        if (X.fmt == FSQR_INT8) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint4 t = __ldcs(reinterpret_cast<const uint4 *>(cp[k]) + ch);
+            const uint32_t tw[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) cw[k][w] = tw[w] & __vcmpleu4(tw[w], 0x02020202u);  // codes > 2 -> 0
+          }
+        } else {  // 2-bit: 16 samples in 4 bytes; widen to one byte per code, code 3 -> 0
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t t = __ldcs(reinterpret_cast<const unsigned *>(cp[k]) + ch);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              const uint32_t b = (t >> (8 * w)) & 0xffu;
+              uint32_t e = (b & 3u) | ((b >> 2 & 3u) << 8) | ((b >> 4 & 3u) << 16) | ((b >> 6) << 24);
+              cw[k][w] = e & ~__vcmpeq4(e, 0x03030303u);
+            }
+          }
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int4 qa = __ldg(qg + ch * 8 + 2 * w);      // samples 4w, 4w+1: (lo, hi), (lo, hi)
+          const int4 qb = __ldg(qg + ch * 8 + 2 * w + 1);  // samples 4w+2, 4w+3
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t x = cw[k][w];
+            const int c0 = (int)(x & 0xffu), c1 = (int)(x >> 8 & 0xffu), c2 = (int)(x >> 16 & 0xffu),
+                      c3 = (int)(x >> 24);
+            ahi[k] += (long long)c0 * qa.y + (long long)c1 * qa.w + (long long)c2 * qb.y + (long long)c3 * qb.w;
+            alo[k] += (long long)c0 * qa.x + (long long)c1 * qa.z + (long long)c2 * qb.x + (long long)c3 * qb.z;
+          }
+        }
+      }
+      const double un = __ldg(unit + g0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        d[k] = un * fma((double)warp_sum_ll(ahi[k]), 67108864.0, (double)warp_sum_ll(alo[k]));
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        double t = 0.0;
+        if (j0 + k < j1) dot_generic<1>(X, j0 + k, u + (int64_t)block_of(bp, G, j0 + k) * npad, lane, &t);
+        d[k] = t;
+      }
+    }
+    if (lane < (int)(j1 - j0)) {
+      const int64_t j = j0 + lane;
+      const int g = block_of(bp, G, j);
+      const double dj = lane == 0 ? d[0] : lane == 1 ? d[1] : lane == 2 ? d[2] : d[3];
+      const double mc = j > X.c ? miss_dot(X, j - 1 - X.c, u + (int64_t)g * npad, 1, 0) : 0.0;
+      s_out[j] = __ldg(X.a + j) * dj + __ldg(X.b + j) * (__ldg(usum + g) - mc);
+    }
+  }
+}
+
+cudaError_t launch_xtv_int(const Dsg &X, const int64_t *block_ptr, int G, const double *u, const int2 *q,
+                           const double *unit, const double *usum, int64_t npad, double *s_out, cudaStream_t s) {
+  if (X.P == 0) return cudaSuccess;
+  const int64_t ngrp = (X.P + 3) >> 2;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (ngrp + kAWarps - 1) / kAWarps;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+  k_xtv_int<<<grid, kAThreads, 0, s>>>(X, block_ptr, G, u, q, unit, usum, npad, s_out);
+  return cudaGetLastError();
+}
+
 // ============================================================= X~ beta
 
 // Partial sums of X~ beta over the active columns listed by the column pass:

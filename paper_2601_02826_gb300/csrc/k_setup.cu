@@ -398,6 +398,146 @@ cudaError_t launch_xv_blocks(const Dsg &X, const double *v, const int64_t *split
   return cudaGetLastError();
 }
 
+// ------------------------------- exact integer products for the setup passes
+//
+// The power method and lambda_max multiply the stored codes (0, 1, 2) by a
+// vector. As FP64 SIMT passes they run at the GB300's FP64 rate, far below
+// HBM. Here the vector is rounded once, per segment, to 52-bit fixed point:
+// w_k = q_k unit_s with unit_s = 2^(e-52), 2^e > max_s |w_k|, and
+// q_k = hi_k 2^26 + lo_k, 0 <= lo_k < 2^26. Sums of code * hi and code * lo
+// are exact in int64 (|sum| < 2^48 for n, column ranges <= 2^20) and become
+// one FP64 value per output: the rounding is that of one FP64 operation on
+// the result, and the vector's own rounding is 2^-53 relative to its largest
+// entry.
+
+// Segment s covers x[bounds[2s] .. bounds[2s+1]), or x[s*seglen .. +seglen)
+// when bounds is NULL. Entries below `first` get
+// q = 0 (columns taken in FP64 by the caller). w_k = x_k * mult_k (mult NULL:
+// 1). Also cst[s] = sum over the quantised entries of cmul_k x_k (cmul,
+// cst NULL: none). One CTA of 256 threads per segment, fixed-order sums.
+__global__ void __launch_bounds__(256) k_fix_seg(const double *x, const double *mult, const double *cmul,
+                                                 const int64_t *bounds, int64_t seglen, int64_t first, int2 *q,
+                                                 double *unit, double *cst) {
+  __shared__ double sh[256];
+  const int sg = blockIdx.x;
+  const int64_t k0 = bounds ? bounds[2 * sg] : (int64_t)sg * seglen;
+  const int64_t k1 = bounds ? bounds[2 * sg + 1] : k0 + seglen;
+  double m = 0.0, c = 0.0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
+    if (k < first) continue;
+    const double w = mult ? x[k] * mult[k] : x[k];
+    m = fmax(m, fabs(w));
+    if (cmul) c = fma(cmul[k], x[k], c);
+  }
+  m = block_max(m, sh);
+  if (cst) {
+    c = block_sum(c, sh);
+    if (threadIdx.x == 0) cst[sg] = c;
+  }
+  // 2^e > m: ilogb(m) = floor(log2 m) for finite m > 0
+  const int e = (m > 0.0 && m <= 1.0e300) ? ilogb(m) + 1 : 0;
+  if (threadIdx.x == 0) unit[sg] = (m > 0.0 && m <= 1.0e300) ? ldexp(1.0, e - 52) : 0.0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
+    long long v = 0;
+    if (k >= first && m > 0.0 && m <= 1.0e300) {
+      const double t = ldexp(mult ? x[k] * mult[k] : x[k], 52 - e);  // |t| < 2^52
+      v = (fabs(t) <= 4503599627370496.0) ? __double2ll_rn(t) : 0LL;
+    }
+    const long long hi = v >> 26;  // arithmetic shift: floor
+    q[k] = make_int2((int)(v - (hi << 26)), (int)hi);
+  }
+}
+
+cudaError_t launch_fix_seg(const double *x, const double *mult, const double *cmul, const int64_t *bounds,
+                           int64_t seglen, int nseg, int64_t first, int2 *q, double *unit, double *cst,
+                           cudaStream_t s) {
+  if (nseg <= 0) return cudaSuccess;
+  k_fix_seg<<<nseg, 256, 0, s>>>(x, mult, cmul, bounds, seglen, first, q, unit, cst);
+  return cudaGetLastError();
+}
+
+// u_g = X~_g v_g with exact integer products over the stored columns (int8 or
+// 2-bit codes; a missing code reads as 0 and k_miss_xv takes its share back
+// out). The split table and the layout of `part` are those of k_xv_split;
+// q/unit/cst are k_fix_seg's output over the splits (mult = a, cmul = b,
+// first = c + 1), so that stored column j adds x_ij q_j unit + b_j v_j.
+// The intercept and the covariates (j <= c) stay in FP64. Thread: 8 samples.
+__global__ void __launch_bounds__(256) k_xv_int(Dsg X, const double *v, const int64_t *splits, const int2 *q,
+                                                const double *unit, const double *cst, double *part,
+                                                int64_t npad) {
+  const int sp = blockIdx.y;
+  const int64_t ja = splits[2 * sp], jb = splits[2 * sp + 1];
+  const int64_t i0 = (int64_t)blockIdx.x * 2048 + threadIdx.x * 8;
+  long long ahi[8], alo[8];
+  double acc[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    ahi[r] = 0;
+    alo[r] = 0;
+    acc[r] = 0.0;
+  }
+  if (i0 < X.n) {
+    int64_t j = ja;
+    for (; j < jb && j <= X.c; ++j) {  // intercept (x~ = b_0) and covariates, FP64
+      const double aj = X.a[j], bj = X.b[j], vj = v[j];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int64_t i = i0 + r;
+        if (i >= X.n) break;
+        const double x = (j == 0) ? 0.0 : X.cov[(j - 1) * X.n + i];
+        acc[r] = fma(fma(aj, x, bj), vj, acc[r]);
+      }
+    }
+    if (X.fmt == FSQR_INT8) {
+      // i0 is a multiple of 8 and i0 + 8 <= pad16(n) <= ld: one aligned 8-byte load
+      for (; j < jb; ++j) {
+        const int2 qj = __ldg(q + j);
+        const uint2 cw = __ldcs(reinterpret_cast<const uint2 *>(X.geno + (j - 1 - X.c) * X.ld + i0));
+        // codes above 2 (missing) read as 0
+        const uint32_t w0 = cw.x & __vcmpleu4(cw.x, 0x02020202u);
+        const uint32_t w1 = cw.y & __vcmpleu4(cw.y, 0x02020202u);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int cd = (int)(((r < 4 ? w0 : w1) >> (8 * (r & 3))) & 0xffu);
+          ahi[r] += (long long)cd * qj.y;
+          alo[r] += (long long)cd * qj.x;
+        }
+      }
+    } else if (X.fmt == FSQR_2BIT) {
+      // 8 samples = 2 bytes at byte i0/4, inside ld (ld >= 2 ceil(n/8))
+      for (; j < jb; ++j) {
+        const int2 qj = __ldg(q + j);
+        const uint32_t cw = __ldcs(reinterpret_cast<const unsigned short *>(X.geno + (j - 1 - X.c) * X.ld + (i0 >> 2)));
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          int cd = (int)((cw >> (2 * r)) & 3u);
+          cd = (cd == 3) ? 0 : cd;
+          ahi[r] += (long long)cd * qj.y;
+          alo[r] += (long long)cd * qj.x;
+        }
+      }
+    }
+  }
+  const double un = unit[sp], cs = cst[sp];
+  double *out = part + (int64_t)sp * npad;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t i = i0 + r;
+    if (i < npad)
+      out[i] = (i < X.n) ? fma(un, fma((double)ahi[r], 67108864.0, (double)alo[r]), cs + acc[r]) : 0.0;
+  }
+}
+
+cudaError_t launch_xv_blocks_int(const Dsg &X, const double *v, const int64_t *splits, const int *split_of_block,
+                                 int G, int nsplit, const int2 *q, const double *unit, const double *cst, double *u,
+                                 int64_t npad, double *part, cudaStream_t s) {
+  dim3 g1((unsigned)((X.n + 2047) / 2048), (unsigned)nsplit);
+  k_xv_int<<<g1, 256, 0, s>>>(X, v, splits, q, unit, cst, part, npad);
+  dim3 g2((unsigned)((npad + 255) / 256), (unsigned)G);
+  k_xv_reduce<<<g2, 256, 0, s>>>(part, split_of_block, G, npad, u);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------- state layout
 
 // dst[j*NB + q] = src[q*lds + j] for q < nb and j < len, 0 for len <= j <

@@ -26,3 +26,15 @@ def to_np(t):
 def max_rel(a, b):
     a, b = np.asarray(a), np.asarray(b)
     return float(np.max(np.abs(a - b)) / (1.0 + np.max(np.abs(b)))) if a.size else 0.0
+
+
+_MEMO = {}
+
+
+def memo(key, fn):
+    """fn() once per key in a test session. The oracle is deterministic, so a
+    converged oracle solve that several parametrised tests compare against
+    (the same problem solved in another precision or slot count) runs once."""
+    if key not in _MEMO:
+        _MEMO[key] = fn()
+    return _MEMO[key]

@@ -9,7 +9,7 @@ import pytest
 from oracle import enet as EN
 from oracle import fsqrppa as O
 from paper_2601_02826_gb300 import synth
-from tests.gpu_helpers import max_rel, to_np
+from tests.gpu_helpers import max_rel, memo, to_np
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -69,7 +69,8 @@ def test_enet_converged_fit_matches_oracle(ctx, precision):
     lam_s = 0.3 * lmax
     gamma = 1.5 * lmax
     lam, gam = lam_s * w.omega, gamma * w.omega
-    ref = EN.fsqrppa_enet(d.Xt, w.y, tau, lam, gam, bp, eta, mu, tol=1e-7, max_iter=900000, lam_norm=lmax)
+    ref = memo(("enet", tau), lambda: EN.fsqrppa_enet(d.Xt, w.y, tau, lam, gam, bp, eta, mu, tol=1e-7,
+                                                      max_iter=900000, lam_norm=lmax))
     assert ref.converged
     b = torch.zeros(w.P, dtype=torch.float64, device="cuda")
     z = torch.zeros(w.n, dtype=torch.float64, device="cuda")

@@ -14,7 +14,7 @@ import pytest
 from oracle import fsqrppa as O
 from oracle import lla as LLA
 from paper_2601_02826_gb300 import synth
-from tests.gpu_helpers import to_np
+from tests.gpu_helpers import memo, to_np
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -43,8 +43,9 @@ def test_one_step_lla_matches_oracle(ctx, penalty, a, precision):
     mu = O.default_mu(w.y)
     bp = w.block_ptr()
     eta = O.eta_blocks(d.Xt, bp, mu)
-    steps, weights = LLA.lla_fit(d.Xt, w.y, tau, lam, w.omega, bp, eta, mu, penalty, a, L=1, tol=1e-6,
-                                 max_iter=900000, lam_norm=lmax)
+    steps, weights = memo(("lla", penalty, a), lambda: LLA.lla_fit(d.Xt, w.y, tau, lam, w.omega, bp, eta, mu,
+                                                                   penalty, a, L=1, tol=1e-6, max_iter=900000,
+                                                                   lam_norm=lmax))
     assert all(s.converged for s in steps)
     # the GPU's first step alone
     b0 = torch.zeros(w.P, dtype=torch.float64, device="cuda")

@@ -16,7 +16,7 @@ import pytest
 
 from oracle import fsqrppa as O
 from paper_2601_02826_gb300 import synth
-from tests.gpu_helpers import max_rel, oracle_problem, to_np
+from tests.gpu_helpers import max_rel, memo, oracle_problem, to_np
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -134,7 +134,8 @@ def test_fp64_converged_fit_matches_oracle(ctx, case, frac):
     dw = _up(ctx, w)
     rc, info, b, z, t = _run(ctx, dw, w, tau, lam_s, mu, eta, 200000, tol=1e-6)
     assert rc == 0 and info.status == 0
-    ref = O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=1e-6, max_iter=200000, lam_norm=lmax)
+    ref = memo(("parity", case, frac), lambda: O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=1e-6,
+                                                         max_iter=200000, lam_norm=lmax))
     assert ref.converged
     assert abs(info.iters - ref.iters) <= 10
     ko = O.kkt(d.Xt, w.y, tau, lam, lmax, b, z, t)
@@ -155,7 +156,8 @@ def test_mixed_converged_fit_matches_oracle(ctx, precision, digits):
     rc, info, b, z, t = _run(ctx, dw, w, tau, lam_s, mu, eta, 200000, tol=1e-6, precision=precision,
                              digits=digits)
     assert rc == 0
-    ref = O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=1e-6, max_iter=200000, lam_norm=lmax)
+    ref = memo(("parity", "int8", 0.3), lambda: O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=1e-6,
+                                                          max_iter=200000, lam_norm=lmax))
     ko = O.kkt(d.Xt, w.y, tau, lam, lmax, b, z, t)
     assert ko.value <= 1e-6 * (1 + 1e-3)
     assert O.objective(d.Xt, w.y, b, tau, lam) == pytest.approx(O.objective(d.Xt, w.y, ref.beta, tau, lam), rel=1e-6)
@@ -261,6 +263,12 @@ def test_batch_grid_and_path_warm_start(ctx):
     lmaxs = [O.lambda_max(d.Xt, w.y, t, w.omega) for t in taus]
     lams = np.array([[f * lm for f in fr] for lm in lmaxs])
     B = len(taus) * len(fr)
+    refs = {}
+    for t_i, tau in enumerate(taus):
+        for l_i in range(len(fr)):
+            lam = lams[t_i, l_i] * w.omega
+            refs[t_i, l_i] = O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=1e-6, max_iter=400000,
+                                       lam_norm=lmaxs[t_i])
     for warm, prec in [(0, 0), (2, 0), (2, 1), (0, 2)]:
         beta = torch.zeros(B * w.P, dtype=torch.float64, device="cuda")
         z = torch.zeros(B * w.n, dtype=torch.float64, device="cuda")
@@ -276,9 +284,8 @@ def test_batch_grid_and_path_warm_start(ctx):
                 lam = lams[t_i, l_i] * w.omega
                 ko = O.kkt(d.Xt, w.y, tau, lam, lmaxs[t_i], bb[f], zz[f], tt[f])
                 assert ko.value <= 1.001e-6, (warm, prec, f, ko)
-                ref = O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=1e-6, max_iter=400000, lam_norm=lmaxs[t_i])
                 assert O.objective(d.Xt, w.y, bb[f], tau, lam) == pytest.approx(
-                    O.objective(d.Xt, w.y, ref.beta, tau, lam), rel=1e-6)
+                    O.objective(d.Xt, w.y, refs[t_i, l_i].beta, tau, lam), rel=1e-6)
                 assert infos[f].status == 0 and infos[f].lambda_max == pytest.approx(lmaxs[t_i], rel=1e-10)
 
 

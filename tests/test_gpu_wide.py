@@ -13,7 +13,7 @@ import pytest
 
 from oracle import fsqrppa as O
 from paper_2601_02826_gb300 import synth
-from tests.gpu_helpers import max_rel, to_np
+from tests.gpu_helpers import max_rel, memo, to_np
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -100,8 +100,8 @@ def test_wide_converged_fits_meet_the_oracle_stop_test(ctx, warm):
             assert ko.value <= 1.001e-6, (f, ko)
             assert infos[f].kkt >= ko.value * (1 - 1e-6), f  # the certified test is an upper bound
             if l_i == 2:
-                ref = O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=1e-6, max_iter=900000,
-                                lam_norm=lmaxs[t_i])
+                ref = memo(("wide", tau, l_i), lambda: O.fsqrppa(d.Xt, w.y, tau, lam, bp, eta, mu, tol=1e-6,
+                                                                 max_iter=900000, lam_norm=lmaxs[t_i]))
                 assert O.objective(d.Xt, w.y, bb[f], tau, lam) == pytest.approx(
                     O.objective(d.Xt, w.y, ref.beta, tau, lam), rel=1e-6)
 
