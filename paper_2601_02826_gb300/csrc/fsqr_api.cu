@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "fsqr_fixed.h"
 #include "fsqr_internal.h"
 
 using namespace fsqr;

@@ -215,21 +215,6 @@ cudaError_t launch_power_step(const double *w, const int64_t *block_ptr, int G, 
 cudaError_t launch_xv_blocks(const Dsg &X, const double *v, const int64_t *splits,
                              const int *split_of_block, int G, int nsplit, double *u,
                              int64_t npad, double *part, cudaStream_t s);
-// Exact integer products for the setup passes (52-bit fixed-point vectors):
-// launch_fix_seg rounds x (times mult) per segment to q = hi 2^26 + lo with
-// unit[s] (and cst[s] = sum cmul_k x_k over the rounded entries), segments
-// from bounds (2 per segment) or of seglen entries; launch_xv_blocks_int is
-// launch_xv_blocks for int8/2-bit storage from q/unit/cst over the splits;
-// launch_xtv_int writes s_out[j] = x~_j^T u_g(j) from u's fixed point per
-// block (G = 1 and block_ptr NULL: one vector for every column).
-cudaError_t launch_fix_seg(const double *x, const double *mult, const double *cmul, const int64_t *bounds,
-                           int64_t seglen, int nseg, int64_t first, int2 *q, double *unit, double *cst,
-                           cudaStream_t s);
-cudaError_t launch_xv_blocks_int(const Dsg &X, const double *v, const int64_t *splits, const int *split_of_block,
-                                 int G, int nsplit, const int2 *q, const double *unit, const double *cst, double *u,
-                                 int64_t npad, double *part, cudaStream_t s);
-cudaError_t launch_xtv_int(const Dsg &X, const int64_t *block_ptr, int G, const double *u, const int2 *q,
-                           const double *unit, const double *usum, int64_t npad, double *s_out, cudaStream_t s);
 cudaError_t launch_pack(const double *src, int64_t lds, double *dst, int64_t len, int nb,
                         int NB, int64_t dst_rows, cudaStream_t s);
 cudaError_t launch_unpack(const double *src, double *dst, int64_t lds, int64_t len, int nb,

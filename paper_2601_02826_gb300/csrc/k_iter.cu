@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "fsqr_device.cuh"
+#include "fsqr_fixed.h"
 #include "fsqr_internal.h"
 
 namespace fsqr {

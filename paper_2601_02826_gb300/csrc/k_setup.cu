@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "fsqr_fixed.h"
 #include "fsqr_internal.h"
 
 namespace fsqr {

@@ -201,7 +201,7 @@ def test_batch_of_eight_fits_on_tensor_cores(ctx):
     dw = _up(ctx, w)
     d = O.build_design(O.decode_stored(w.geno, w.fmt, w.n), w.cov)
     taus = [0.15, 0.4, 0.6, 0.85]
-    fr = [0.5, 0.25]
+    fr = [0.3, 0.15]
     lmaxs = [O.lambda_max(d.Xt, w.y, t, w.omega) for t in taus]
     lams = np.array([[f * lm for f in fr] for lm in lmaxs])
     B = 8
@@ -227,7 +227,7 @@ def test_autotuned_group_size(ctx):
     dw = _up(ctx, w)
     d = O.build_design(O.decode_stored(w.geno, w.fmt, w.n), w.cov)
     taus = [0.3, 0.5, 0.7]
-    fr = [0.5, 0.35]
+    fr = [0.3, 0.2]
     lmaxs = [O.lambda_max(d.Xt, w.y, t, w.omega) for t in taus]
     lams = np.array([[f * lm for f in fr] for lm in lmaxs])
     B = 6
