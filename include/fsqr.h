@@ -195,7 +195,11 @@ int fsqr_col_stats(fsqr_ctx *ctx, const fsqr_design *X, double *mean_out, double
 /* lambda_max(tau) = max_{j>=1, omega_j>0} |x~_j^T v| / (n omega_j) with
  * v_i = tau - 1{y_i < y_(ceil(n tau))}: the smallest lambda at which
  * beta_{1..} = 0 is optimal up to ties (penalty path, Section 7).
- * y, omega: device (omega length P). out: host scalar. */
+ * y, omega: device (omega length P). out: host scalar.
+ * For int8 and 2-bit storage x~_j^T v is an exact integer sum of the codes
+ * with v rounded once to 52-bit fixed point (the accuracy of FP64
+ * arithmetic); dense storage computes it in FP64. The same holds for the
+ * power method of fsqr_eta. */
 int fsqr_lambda_max(fsqr_ctx *ctx, const fsqr_design *X, const double *y, double tau,
                     const double *omega, double *out);
 
