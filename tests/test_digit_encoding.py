@@ -15,10 +15,9 @@ against the FP8 E4M3 format definition (1 sign bit, 4 exponent bits with bias
     int64 sums of codes times hi and lo cannot overflow, and a power method
     that rounds its vectors this way gives the oracle's estimates.
 """
+import math
 import os
 import re
-
-import math
 
 import numpy as np
 

@@ -1,9 +1,10 @@
 """Sequential strong-rule screening along the lambda path (opts.screen) on
 the GPU against the oracle: every screened fit meets the oracle's stop test
 on the FULL design, its objective is within the stop test's reach of the
-exact optimum (an LP solve), and the screened solves stream fewer columns. Also the paper's sparse simulation
-design (Section 7.1) as a statistical sanity check of a screened path with
-HBIC selection: the selected fit finds the true effects.
+exact optimum (an LP solve), and the screened solves stream fewer columns.
+Also the paper's sparse simulation design (Section 7.1) as a statistical
+sanity check of a screened path with HBIC selection: the selected fit finds
+the true effects.
 """
 import numpy as np
 import pytest
