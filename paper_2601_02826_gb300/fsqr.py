@@ -207,9 +207,11 @@ class Context:
 
     # ---------------------------------------------------------- functions
     def col_stats(self, d, mean_out, sd_out):
+        """fsqr_col_stats: column means and population sds (standardisation, Section 7)."""
         self._check(self.L.fsqr_col_stats(self.h, C.byref(d), _ptr(mean_out), _ptr(sd_out)))
 
     def lambda_max(self, d, y, tau, omega) -> float:
+        """fsqr_lambda_max: the smallest lambda with beta_{1..} = 0 optimal (penalty path, Section 7)."""
         out = C.c_double()
         self._check(self.L.fsqr_lambda_max(self.h, C.byref(d), _ptr(y), tau, _ptr(omega), C.byref(out)))
         return out.value
@@ -223,6 +225,7 @@ class Context:
         return out.value
 
     def eta(self, d, block_ptr, mu, margin=0.05, max_iter=100, tol=1e-6) -> np.ndarray:
+        """fsqr_eta: eta_g = (1 + margin) mu Lambda_hat(X~_g^T X~_g) by the power method (Section 4)."""
         bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
         G = len(bp) - 1
         out = np.zeros(max(G, 1))
@@ -241,6 +244,7 @@ class Context:
 
     def fit(self, d, y, tau, lam, omega, block_ptr, beta, z, theta, opts=None,
             allowed=(OK, ENOCONV, ETIMEOUT)):
+        """fsqr_fit: one FS-QRPPA fit (Algorithm 1); beta, z, theta receive the result (and hold the start when opts warm = 1)."""
         bp = np.ascontiguousarray(block_ptr, dtype=np.int64)
         G = len(bp) - 1
         o, keep = self._opts(opts, G)
@@ -253,6 +257,7 @@ class Context:
 
     def fit_batch(self, d, y, taus, lambdas, omega, block_ptr, beta, z, theta, opts=None,
                   allowed=(OK, ENOCONV, ETIMEOUT), host=False):
+        """fsqr_fit_batch (host=True: fsqr_fit_batch_host): a tau x lambda grid of fits."""
         taus = np.ascontiguousarray(taus, dtype=np.float64)
         lam = np.ascontiguousarray(lambdas, dtype=np.float64)
         n_tau = len(taus)
@@ -306,6 +311,7 @@ class Context:
         return cov.value, wid.value, cr.value
 
     def kkt(self, d, y, tau, lam, omega, lam_norm, beta, z, theta) -> Info:
+        """fsqr_kkt: stop-test residuals, primal, dual and gap of a given iterate (Proposition 1)."""
         info = Info()
         self._check(self.L.fsqr_kkt(self.h, C.byref(d), _ptr(y), tau, lam, _ptr(omega), lam_norm,
                                     _ptr(beta), _ptr(z), _ptr(theta), C.byref(info)))
@@ -314,21 +320,26 @@ class Context:
     # ---- learned warm start (float32 device tensors for the network)
 
     def mlp_param_count(self) -> int:
+        """fsqr_mlp_param_count: floats in the warm-start network."""
         return int(self.L.fsqr_mlp_param_count())
 
     def mlp_init(self, params, seed: int):
+        """fsqr_mlp_init: seeded initial parameters of the warm-start network."""
         self._check(self.L.fsqr_mlp_init(self.h, _ptr(params), seed))
 
     def mlp_forward(self, params, x, out):
+        """fsqr_mlp_forward: the network on the rows of x (FP32, device)."""
         self._check(self.L.fsqr_mlp_forward(self.h, _ptr(params), _ptr(x), x.shape[0], _ptr(out)))
 
     def mlp_grad(self, params, x, t, w, grad) -> float:
+        """fsqr_mlp_grad: weighted squared loss and its gradient; returns the loss."""
         loss = C.c_double()
         self._check(self.L.fsqr_mlp_grad(self.h, _ptr(params), _ptr(x), _ptr(t), _ptr(w), x.shape[0],
                                          _ptr(grad), C.byref(loss)))
         return loss.value
 
     def mlp_train(self, params, m, v, step0, x, t, w, steps, batch, lr, seed) -> np.ndarray:
+        """fsqr_mlp_train: Adam steps on batches drawn on the device; returns the losses."""
         losses = np.zeros(max(steps, 1))
         self._check(self.L.fsqr_mlp_train(self.h, _ptr(params), _ptr(m), _ptr(v), step0, _ptr(x), _ptr(t),
                                           _ptr(w), x.shape[0], steps, batch, lr, seed,
@@ -336,22 +347,27 @@ class Context:
         return losses[:steps]
 
     def warm_features(self, d, y, tau, lam_frac, omega, u) -> float:
+        """fsqr_warm_features: the network inputs of every feature column; returns lambda_max."""
         lmax = C.c_double()
         self._check(self.L.fsqr_warm_features(self.h, C.byref(d), _ptr(y), tau, lam_frac, _ptr(omega), _ptr(u),
                                               C.byref(lmax)))
         return lmax.value
 
     def warm_start(self, d, y, tau, lam_frac, omega, params, beta, z, theta):
+        """fsqr_warm_start: the start (beta, z, theta) the network proposes for one fit."""
         self._check(self.L.fsqr_warm_start(self.h, C.byref(d), _ptr(y), tau, lam_frac, _ptr(omega),
                                            _ptr(params), _ptr(beta), _ptr(z), _ptr(theta)))
 
     def predict(self, d, beta, B, out):
+        """fsqr_predict: x~_i^T beta of B coefficient vectors (Section 7.1)."""
         self._check(self.L.fsqr_predict(self.h, C.byref(d), _ptr(beta), B, _ptr(out)))
 
     def back_transform(self, d, beta_std, B, out):
+        """fsqr_back_transform: standardised coefficients on the original scale (Section 7)."""
         self._check(self.L.fsqr_back_transform(self.h, C.byref(d), _ptr(beta_std), B, _ptr(out)))
 
     def profile(self, enable: bool | None = None, reset: bool = False) -> Profile:
+        """fsqr_profile_*: switch kernel sampling, read the counters, optionally reset them."""
         if enable is not None:
             self.L.fsqr_profile_enable(self.h, 1 if enable else 0)
         if reset:
@@ -368,4 +384,5 @@ class Context:
         return rc, ok.value
 
     def last_error(self) -> str:
+        """fsqr_last_error: message of the last failed call."""
         return self.L.fsqr_last_error(self.h).decode()
