@@ -332,6 +332,8 @@ def run_gb300(args, rank, world, local_rank):
     # accuracy of the returned fits (their own stop test) and iteration counts
     iters = [i.iters for i in infos[-B:]]
     kkts = [i.kkt for i in infos[-B:]]
+    # set-up inside each timed solve (column statistics, eta), reported apart
+    setup_ms = [i.t_setup_ms for i in infos[::B]]
 
     # plain FP64 GPU FS-QRPPA: one fit at a time, cold start (comparison).
     # Per-iteration time from two run lengths (their difference removes the
@@ -402,6 +404,7 @@ def run_gb300(args, rank, world, local_rank):
                        "xbeta_and_vector_update": kprof.xb_ms / max(1, kprof.xb_samples),
                        "vec": (kprof.vec_ms / kprof.vec_samples) if kprof.vec_samples else None},
         "iters": iters, "kkt": kkts, "iterations_timed": prof.iterations,
+        "setup_ms_per_step": float(np.mean(setup_ms)) if setup_ms else None,
         "gpu_launches": int(prof.kernel_launches),
         "clocks": clocks.summary(),
         "e2e": e2e,
